@@ -1,0 +1,351 @@
+"""Benchmark: all-node effective-resistance map throughput (nodes/s) on one GB300 per rank.
+
+One step = the whole hot path on one synthetic network already resident in HBM:
+JL sketch (er_sketch) + k-RHS Jacobi-PCG solve (er_solve) + R map (er_reff_map).
+Default workload: 4 tiers x 512x512 (1,048,576 nodes), k = 256, FP32 storage with
+FP64-accurate dots, FP64 residual replacement and restart sweeps.
+
+Prints one JSON line (rank 0).  N > 1 (torchrun): every rank maps its own network
+(independent seeds) with no collective on the data path; value = all ranks' nodes /
+the slowest rank's time (weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--prec fp32|fp64] [--no-accuracy]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "R_eff map nodes/s at <=1e-3 max rel err (FP32+refinement vs plain FP64)"
+UNIT = "nodes/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="precision_4x512x512")
+    p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--k", type=int, default=256)
+    p.add_argument("--tol", type=float, default=None)
+    p.add_argument("--no-accuracy", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=256, help="W=H of the oracle's bounded sample")
+    return p.parse_args()
+
+
+def make_workload(name, rank=0):
+    from paper_2607_05818_gb300 import instances as I
+    if name not in I.WORKLOADS:
+        raise SystemExit(f"unknown workload {name}; choose from {sorted(I.WORKLOADS)}")
+    fn = I.WORKLOADS[name]
+    inst = fn() if rank == 0 else fn(seed=I.BASE_SEED + 1000 + rank)
+    return inst
+
+
+def cpu_sample_instance(W):
+    """The bounded sample the oracle is timed on: the 4-tier precision recipe at W x W with
+    TSV and cluster counts scaled by area."""
+    from paper_2607_05818_gb300 import instances as I
+    f = (W / 512) ** 2
+    return I.precision_4x512(W=W, H=W, n_tsv=max(1, int(round(2000 * f))), n_clusters=max(1, int(round(40 * f))))
+
+
+def oracle_step(inst, k, seed):
+    """The CPU oracle as it stands: sparse factorisation, sketch, k-RHS solves, row norms."""
+    from oracle import exact
+    from oracle import sketch as osk
+    t0 = time.perf_counter()
+    f = exact.SparseFactor(inst)
+    Yt = osk.sketch(inst, k, seed)
+    Z = f.solve(Yt)
+    R = np.sum(Z * Z, axis=1)
+    R[f.floating] = np.inf
+    return time.perf_counter() - t0, int(np.sum(~f.floating))
+
+
+def cpu_baseline(args):
+    from oracle import build as ob
+    ob.build()
+    inst = cpu_sample_instance(args.cpu_sample)
+    dt, n_ok = oracle_step(inst, args.k, inst.meta.get("seed", 1))
+    return {"value": n_ok / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one {inst.T}x{inst.W}x{inst.H} network ({inst.n} nodes) of the same recipe, k={args.k}: "
+                      f"SuperLU factorisation + C sketch + {args.k} sparse solves + row norms, "
+                      f"single-threaded, {dt:.1f} s"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts):
+            return parts[local_rank].strip()
+    return str(local_rank)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("er_pcg.cu", "er_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2607_05818_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel source has changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel, {})
+    if e.get("source_hash") != kernel_source_hash() or e.get("workload") != workload:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2607_05818_gb300 import er
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    inst = make_workload(args.workload, rank)
+    k = args.k
+    seed = int(inst.meta.get("seed", 1))
+    prec = args.prec
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    es = 4 if prec == "fp32" else 8
+    g = er.grid_create(inst)
+    info = g.info()
+    n_ok = info["n_nodes"] - info["n_floating"]
+    Yt = torch.empty((inst.n, k), dtype=dt, device=dev)
+    Z = torch.empty_like(Yt)
+    R = torch.empty(inst.n, dtype=torch.float64, device=dev)
+    opts = er.default_solve_opts(prec)
+    if args.tol is not None:
+        opts.tol = args.tol
+    opts.profile = 1
+    stream = torch.cuda.current_stream()
+
+    def step():
+        er.sketch(g, k, seed, prec, Yt)
+        _, st = er.solve(g, Yt, Z, k, prec, opts)
+        er.reff_map(g, Z, k, prec, R)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    stats = []
+    with ClockSampler(gpu_index(local_rank)) as clk:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step())
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        nt = torch.tensor([float(n_ok)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(nt)
+        n_total = float(nt.item())
+    else:
+        n_total = float(n_ok)
+    value = n_total * args.steps / (ms / 1e3)
+
+    # per-pass durations measured live (CUDA events on the solver stream) in the timed region
+    launches = np.sum([s["launches"] for s in stats], axis=0)
+    kms = np.sum([s["kernel_ms"] for s in stats], axis=0)
+    iters = [s["iterations"] for s in stats]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_note = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    nk = inst.n * k
+    coef = 16 * inst.n  # cE, cS and two TSV row pointers per node
+    per = {  # algorithmic bytes per launch of each pass
+        "A": (2 * nk * es + coef) if prec == "fp32" else (4 * nk * es + coef),
+        "B": (6 * nk * es + coef) if prec == "fp32" else (6 * nk * es),
+    }
+    names = {"A": "k_stencil<float,float,MODE_A_DOT>" if prec == "fp32" else "k_stencil<double,double,MODE_A_STORE>",
+             "B": "k_stencil<float,float,MODE_B>" if prec == "fp32" else "k_stream<double,MODE_S>"}
+    rl = []
+    for key, idx in (("B", 1), ("A", 0)):
+        n_l = int(launches[idx])
+        avg_ms = float(kms[idx]) / max(n_l, 1)
+        ach = per[key] / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
+        rl.append({"kernel": names[key], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                   "frac": (ach / peak) if ach else None, "traffic": ncu_traffic(names[key], args.workload),
+                   "algorithmic_bytes_per_launch": per[key], "avg_launch_ms": avg_ms, "launches": n_l,
+                   "share_of_step": float(kms[idx]) / ms if ms > 0 else None, "peak_source": peak_note})
+    gpu_launches = int(launches.sum()) + 2 * args.steps  # + sketch and reff_map per step
+
+    result = {"rank0_iterations": iters, "stats_last": stats[-1]}
+    acc = None
+    if rank == 0 and not args.no_accuracy and prec == "fp32":
+        # accuracy of this form against plain FP64 on the same network and seed (outside timing)
+        Y64 = torch.empty((inst.n, k), dtype=torch.float64, device=dev)
+        Z64 = torch.empty_like(Y64)
+        R64 = torch.empty_like(R)
+        er.sketch(g, k, seed, "fp64", Y64)
+        _, st64 = er.solve(g, Y64, Z64, k, "fp64")
+        er.reff_map(g, Z64, k, "fp64", R64)
+        torch.cuda.synchronize()
+        a, b = R.cpu().numpy(), R64.cpu().numpy()
+        fin = np.isfinite(b)
+        rel = np.abs(a[fin] / b[fin] - 1)
+        acc = {"vs": "plain FP64 GPU PCG (tol 1e-12), same network and seed", "max_rel_err": float(rel.max()),
+               "mean_rel_err": float(rel.mean()), "fp64_iterations": st64["iterations"],
+               "fp64_solve_s": st64["seconds"]}
+        del Y64, Z64, R64
+    # end to end through the host entry point: host arrays in, host R out (copies inside)
+    e2e = None
+    if rank == 0:
+        opts_e = er.default_solve_opts(prec)
+        if args.tol is not None:
+            opts_e.tol = opts.tol
+        R_host = np.empty(inst.n)
+        t0 = time.perf_counter()
+        er.reff_map_host(inst, k, seed, prec, opts_e, R_host)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": n_ok / e2e_s, "unit": UNIT, "h2d_bytes_per_step": info["h2d_bytes"],
+               "d2h_bytes_per_step": inst.n * 8, "seconds": e2e_s,
+               "note": "er_reff_map_host: host assembly + H2D + sketch + solve + map + D2H of R"}
+    return value, ms, result, rl, gpu_launches, clk.summary(), acc, e2e, n_total
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        # the reference arm is the CPU oracle as it stands, rank 0 only
+        if rank != 0:
+            return
+        from oracle import build as ob
+        ob.build()
+        inst = cpu_sample_instance(args.cpu_sample)
+        for _ in range(args.warmup):
+            oracle_step(inst, args.k, 1)
+        ts = []
+        n_ok = 0
+        for _ in range(args.steps):
+            dt, n_ok = oracle_step(inst, args.k, 1)
+            ts.append(dt)
+        tot = sum(ts)
+        v = n_ok * args.steps / tot
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "k": args.k,
+                                            "sample": f"{inst.T}x{inst.W}x{inst.H}"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one {inst.T}x{inst.W}x{inst.H} network of the same recipe per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    value, ms, result, rl, launches, clocks, acc, e2e, n_total = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        cpu = cpu_baseline(args) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "k": args.k, "precision": args.prec,
+                       "nodes_per_rank": int(n_total / world),
+                       "l2": "inputs larger than L2 (each [n][k] array is 1 GiB)",
+                       "iterations_per_step": result["rank0_iterations"]},
+            "roofline": rl[0], "roofline_other": rl[1:], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "accuracy": acc,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * er.h - C ABI of the GB300 effective-resistance library (liber.so).
+ *
+ * Computes every node's effective resistance to the supply, R_i = e_i^T G^-1 e_i,
+ * for a multi-tier 3D-IC power delivery network: per-tier resistive meshes, TSV
+ * segments between adjacent tiers and pads to an ideal, grounded supply.
+ * Effective resistance is defined in the paper's Sec. II-B, Eq. 2
+ * (R(a,b) = (e_a - e_b)^T L^+ (e_a - e_b)); with the supply as node b and its
+ * row/column of L deleted, that is R_i = (G^-1)_ii with G = B^T W B + D, the MNA
+ * conductance matrix of Sec. II-A, Eq. 1.  The network model (tiers joined by
+ * TSV segments Rt_k^{i,i+1}, bumps/pads to the supply) is the paper's Sec. III-A/B.
+ *
+ * The all-node map is computed as
+ *   Y^T = M^T Q^T            (er_sketch; M = [W^{1/2} B; D^{1/2}], Q Rademacher)
+ *   Z   = G^-1 Y^T           (er_solve; k right-hand sides, Jacobi-PCG)
+ *   R_i = ||Z_i||^2          (er_reff_map)
+ * The sketch and the CG solve are not in the paper (it uses a reduced TSV system
+ * for bump-load pairs, Sec. III-C/D); they reach the Eq. 2 quantity for all
+ * nodes at once.
+ *
+ * Conventions (every entry point):
+ *  - Node id i = (t*H + y)*W + x: tier-major, x fastest.  Node-by-RHS arrays are
+ *    row-major [n][k] (the k right-hand sides of a node are contiguous).
+ *  - Device arrays are plain device pointers owned by the caller, 16-byte aligned;
+ *    k must be a positive multiple of 4.  FP64 arrays for ER_FP64, FP32 for
+ *    ER_FP32_REFINE (R is always FP64).
+ *  - Host arrays are owned by the caller and copied before the call returns.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  er_sketch and
+ *    er_reff_map are asynchronous on it; er_grid_create and er_solve synchronise
+ *    it (the solve polls convergence from the host).
+ *  - Errors are returned as er_status; nothing is thrown across the ABI.  Invalid
+ *    arguments are rejected on the host before any launch.  er_last_error()
+ *    returns a thread-local message for the last failing call of this thread.
+ */
+#ifndef ER_H
+#define ER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ER_OK = 0,
+    ER_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or conductance */
+    ER_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in er_last_error) */
+    ER_ERR_OOM = 3,           /* device allocation failed */
+    ER_ERR_NO_SUPPLY = 4,     /* the network has no pad: G is singular everywhere */
+    ER_ERR_NOT_CONVERGED = 5, /* er_solve hit maxit; Z holds the last iterate */
+    ER_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+    ER_WARN_FLOATING = 7      /* success, but some nodes have no path to a pad: R = +inf */
+} er_status;
+
+typedef enum {
+    ER_FP64 = 0,        /* FP64 storage and arithmetic throughout */
+    ER_FP32_REFINE = 1  /* FP32 storage/stencil/updates, FP64-accurate dot products,
+                           FP64 true-residual replacement and restart sweeps */
+} er_precision;
+
+/* One tier: a W x H mesh.  gx[y*(W-1) + x] is the conductance (siemens) of segment
+ * (x,y)-(x+1,y); gy[y*W + x] that of (x,y)-(x,y+1).  0 means open (no segment);
+ * negative or non-finite values are rejected.  All tiers must share W and H. */
+typedef struct {
+    int32_t W, H;
+    const double *gx; /* H*(W-1) entries (may be NULL when W == 1) */
+    const double *gy; /* (H-1)*W entries (may be NULL when H == 1) */
+} er_tier;
+
+/* A TSV segment joining (tier, x, y) and (tier+1, x, y) with conductance g > 0.
+ * A through-stack TSV column is T-1 such segments.  Duplicates act in parallel. */
+typedef struct {
+    int32_t tier, x, y;
+    double g;
+} er_tsv;
+
+/* A pad joining (tier, x, y) to the grounded supply with conductance g > 0. */
+typedef struct {
+    int32_t tier, x, y;
+    double g;
+} er_pad;
+
+typedef struct er_grid er_grid; /* opaque; owned by the library */
+
+typedef struct {
+    int32_t device;       /* CUDA device ordinal; -1 = the current device */
+    int32_t reserved[7];  /* zero */
+} er_options;
+
+typedef struct {
+    double tol;            /* per-column stop: ||D^-1/2 r_j|| <= tol * ||D^-1/2 b_j||
+                              (Jacobi-weighted residual; see er_solve) */
+    int32_t maxit;         /* iteration cap (both forms, all sweeps together) */
+    int32_t check_every;   /* host convergence poll period in iterations (>= 1) */
+    int32_t replace_every; /* ER_FP32_REFINE: FP64 true-residual replacement period m */
+    int32_t max_sweeps;    /* ER_FP32_REFINE: restarts allowed when the FP32 recursion
+                              claims convergence but the FP64 residual disagrees */
+    int32_t use_graph;     /* 1: replay each poll period from a captured CUDA graph */
+    int32_t profile;       /* 1: time every pass with CUDA events on the solver's stream
+                              (disables graphs); fills er_solve_stats.kernel_ms */
+    int32_t reserved[2];   /* zero */
+} er_solve_opts;
+
+/* Pass kinds counted in er_solve_stats.launches / kernel_ms. */
+enum { ER_PASS_A = 0,      /* stencil pass: p' = r + beta p, q = G~ p', dot p'.q */
+       ER_PASS_B = 1,      /* update pass: x, r (and p' in the FP32 form), dot r.r */
+       ER_PASS_R = 2,      /* FP64 true-residual pass */
+       ER_PASS_OTHER = 3,  /* initialisation and final unscaling */
+       ER_N_PASS = 4 };
+
+typedef struct {
+    int32_t iterations;       /* PCG iterations run */
+    int32_t sweeps;           /* restart sweeps (ER_FP32_REFINE) */
+    int32_t converged_cols;   /* columns meeting tol at the end */
+    int32_t k;
+    double max_rel_residual;  /* final FP64 true residual, max over columns, same norm as tol */
+    double seconds;           /* host wall time of the call */
+    int32_t launches[ER_N_PASS];  /* kernels launched, by pass kind */
+    double kernel_ms[ER_N_PASS];  /* summed CUDA-event durations by pass kind (profile = 1) */
+} er_solve_stats;
+
+/* Default solve options: tol 1e-12 (FP64) / 1e-6 (FP32), maxit 100000,
+ * check_every 10, replace_every 50, max_sweeps 8, use_graph 1, profile 0. */
+er_solve_opts er_default_solve_opts(er_precision prec);
+
+/* Build the device-resident grid: per-node couplings of the Jacobi-scaled matrix
+ * D^-1/2 G D^-1/2 (tier-major layout, FP64 and FP32 copies), TSV adjacency as CSR,
+ * raw conductances and canonical edge ids for the sketch, and the floating-node
+ * mask (nodes without a conducting path to a pad; union-find on the host).
+ * Returns ER_OK, ER_WARN_FLOATING (grid usable, those nodes get R = +inf),
+ * ER_ERR_NO_SUPPLY, ER_ERR_INVALID_ARG, ER_ERR_OOM or ER_ERR_CUDA.  *out is set
+ * only on success/warning.  Synchronises `stream`. */
+er_status er_grid_create(const er_tier *tiers, int32_t n_tiers,
+                         const er_tsv *tsv, int64_t n_tsv,
+                         const er_pad *pads, int64_t n_pads,
+                         const er_options *opt, void *stream, er_grid **out);
+
+/* Free the grid and its cached solve workspace.  NULL is accepted. */
+er_status er_grid_destroy(er_grid *g);
+
+/* Sizes: n = T*W*H nodes, floating-node count, number of canonical edge slots
+ * (mesh segment slots + TSV segments + pads), and the bytes er_grid_create copied
+ * host-to-device.  Any output pointer may be NULL. */
+er_status er_grid_info(const er_grid *g, int64_t *n_nodes, int64_t *n_floating,
+                       int64_t *n_edges, int64_t *h2d_bytes);
+
+/* JL sketch Y^T = M^T Q^T into device array Yt [n][k] (FP64 or FP32 by `prec`).
+ * Q[j][e] = +-1/sqrt(k), sign = top bit of SplitMix64(SplitMix64(seed) XOR (e*2^32 + j))
+ * (0 -> +); e is the canonical edge id: x-segment slots (t*H+y)*(W-1)+x, then
+ * y-segment slots (t*(H-1)+y)*W+x, then TSV segments and pads in input order.
+ * Row e of M is +sqrt(w_e) at the lower node id and -sqrt(w_e) at the higher one
+ * (pads: +sqrt(g)).  Rows of floating nodes are written as 0.  Async on `stream`. */
+er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt,
+                    void *stream);
+
+/* Solve G Z = Yt for k right-hand sides (device arrays [n][k], Z written).
+ * Jacobi-preconditioned CG, run as CG on D^-1/2 G D^-1/2 (identical iterates),
+ * X0 = 0, each column stopped when its Jacobi-weighted residual meets opts->tol
+ * and then frozen.  ER_FP32_REFINE keeps FP32 vectors, accumulates dot products
+ * in double-float, recomputes the true residual in FP64 every replace_every
+ * iterations and restarts columns whose FP64 residual misses tol.  The library
+ * allocates (and caches on the grid) its workspace.  opts/stats may be NULL.
+ * Returns ER_ERR_NOT_CONVERGED at maxit (Z valid, stats filled).  Synchronises. */
+er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec,
+                   const er_solve_opts *opts, er_solve_stats *stats, void *stream);
+
+/* R_i = sum_j Z_ij^2 into device array R [n] (FP64); +inf for floating nodes.
+ * Z is FP64 or FP32 per `prec`.  Async on `stream`. */
+er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R,
+                      void *stream);
+
+/* One call from host data to the host R map: create the grid, sketch, solve, map,
+ * copy R [n] (FP64) back to R_host, destroy.  Device memory comes from a cached
+ * per-device pool (er_release_pool frees it).  stats may be NULL. */
+er_status er_reff_map_host(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv,
+                           int64_t n_tsv, const er_pad *pads, int64_t n_pads, int32_t k,
+                           uint64_t seed, er_precision prec, const er_solve_opts *opts,
+                           double *R_host, er_solve_stats *stats, void *stream);
+
+/* Free the cached device pool of er_reff_map_host on the current device. */
+er_status er_release_pool(void);
+
+const char *er_status_str(er_status s);
+const char *er_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ER_H */

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of liber.so (argument marshalling only).
+
+Every call goes straight to the C ABI declared in include/er.h; all arithmetic runs
+in the library's CUDA kernels.  PyTorch is used only to hand over device memory and
+the current CUDA stream.  Importing this module loads the shared library and raises
+ImportError if it has not been built (``__graft_entry__.build()``): there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int32, c_int64, c_uint64, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liber.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+ER_OK, ER_ERR_INVALID_ARG, ER_ERR_CUDA, ER_ERR_OOM, ER_ERR_NO_SUPPLY, ER_ERR_NOT_CONVERGED, \
+    ER_ERR_TIMEOUT, ER_WARN_FLOATING = range(8)
+ER_FP64, ER_FP32_REFINE = 0, 1
+PRECISIONS = {"fp64": ER_FP64, "fp32": ER_FP32_REFINE, ER_FP64: ER_FP64, ER_FP32_REFINE: ER_FP32_REFINE}
+
+
+class er_tier(ctypes.Structure):
+    _fields_ = [("W", c_int32), ("H", c_int32), ("gx", c_void_p), ("gy", c_void_p)]
+
+
+class er_tsv(ctypes.Structure):
+    _fields_ = [("tier", c_int32), ("x", c_int32), ("y", c_int32), ("g", c_double)]
+
+
+class er_pad(ctypes.Structure):
+    _fields_ = [("tier", c_int32), ("x", c_int32), ("y", c_int32), ("g", c_double)]
+
+
+class er_options(ctypes.Structure):
+    _fields_ = [("device", c_int32), ("reserved", c_int32 * 7)]
+
+
+class er_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("maxit", c_int32), ("check_every", c_int32),
+                ("replace_every", c_int32), ("max_sweeps", c_int32), ("use_graph", c_int32),
+                ("profile", c_int32), ("reserved", c_int32 * 2)]
+
+
+class er_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("sweeps", c_int32), ("converged_cols", c_int32),
+                ("k", c_int32), ("max_rel_residual", c_double), ("seconds", c_double),
+                ("launches", c_int32 * 4), ("kernel_ms", c_double * 4)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["launches"] = list(self.launches)
+        d["kernel_ms"] = list(self.kernel_ms)
+        return d
+
+
+PASS_A, PASS_B, PASS_R, PASS_OTHER = range(4)
+
+
+_S = c_int32  # er_status
+_sig = {
+    "er_default_solve_opts": (er_solve_opts, [c_int32]),
+    "er_grid_create": (_S, [POINTER(er_tier), c_int32, POINTER(er_tsv), c_int64, POINTER(er_pad), c_int64,
+                            POINTER(er_options), c_void_p, POINTER(c_void_p)]),
+    "er_grid_destroy": (_S, [c_void_p]),
+    "er_grid_info": (_S, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
+    "er_sketch": (_S, [c_void_p, c_int32, c_uint64, c_int32, c_void_p, c_void_p]),
+    "er_solve": (_S, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(er_solve_opts),
+                      POINTER(er_solve_stats), c_void_p]),
+    "er_reff_map": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "er_reff_map_host": (_S, [POINTER(er_tier), c_int32, POINTER(er_tsv), c_int64, POINTER(er_pad), c_int64,
+                              c_int32, c_uint64, c_int32, POINTER(er_solve_opts), c_void_p,
+                              POINTER(er_solve_stats), c_void_p]),
+    "er_release_pool": (_S, []),
+    "er_status_str": (ctypes.c_char_p, [c_int32]),
+    "er_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class ErError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.er_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_lib.er_status_str(status).decode()} ({msg})")
+
+
+def _check(status, where, ok=(ER_OK, ER_WARN_FLOATING)):
+    if status not in ok:
+        raise ErError(status, where)
+    return status
+
+
+def status_str(s) -> str:
+    return _lib.er_status_str(s).decode()
+
+
+def default_solve_opts(prec="fp64", **over) -> er_solve_opts:
+    o = _lib.er_default_solve_opts(PRECISIONS[prec])
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------------ marshalling
+
+_SEG = np.dtype([("tier", "<i4"), ("x", "<i4"), ("y", "<i4"), ("g", "<f8")], align=True)
+assert _SEG.itemsize == ctypes.sizeof(er_tsv) == ctypes.sizeof(er_pad)
+
+
+class _Marshalled:
+    """ctypes views of one network instance (keeps the numpy buffers alive)."""
+
+    def __init__(self, inst):
+        T, W, H = inst.T, inst.W, inst.H
+        self.gx = [np.ascontiguousarray(inst.gx[t], dtype=np.float64) for t in range(T)]
+        self.gy = [np.ascontiguousarray(inst.gy[t], dtype=np.float64) for t in range(T)]
+        self.tiers = (er_tier * T)()
+        for t in range(T):
+            self.tiers[t].W, self.tiers[t].H = W, H
+            self.tiers[t].gx = self.gx[t].ctypes.data if self.gx[t].size else None
+            self.tiers[t].gy = self.gy[t].ctypes.data if self.gy[t].size else None
+        self.nt, self.npd = len(inst.tsv_g), len(inst.pad_g)
+        self._tsv = self._segments(inst.tsv_tier, inst.tsv_x, inst.tsv_y, inst.tsv_g)
+        self._pads = self._segments(inst.pad_tier, inst.pad_x, inst.pad_y, inst.pad_g)
+        self.tsv = ctypes.cast(self._tsv.ctypes.data, POINTER(er_tsv))
+        self.pads = ctypes.cast(self._pads.ctypes.data, POINTER(er_pad))
+        self.T = T
+
+    @staticmethod
+    def _segments(tier, x, y, g):
+        a = np.zeros(max(len(g), 1), dtype=_SEG)
+        if len(g):
+            a["tier"], a["x"], a["y"], a["g"] = tier, x, y, g
+        return a
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Grid:
+    """An er_grid handle (device-resident network)."""
+
+    def __init__(self, inst, device: int = -1, stream=None):
+        m = _Marshalled(inst)
+        opt = er_options()
+        opt.device = device
+        h = c_void_p()
+        self.status = _check(_lib.er_grid_create(m.tiers, m.T, m.tsv, m.nt, m.pads, m.npd, ctypes.byref(opt),
+                                                 _stream(stream), ctypes.byref(h)), "er_grid_create")
+        self.handle = h
+        self.T, self.W, self.H = inst.T, inst.W, inst.H
+
+    def info(self):
+        n, f, e, b = c_int64(), c_int64(), c_int64(), c_int64()
+        _check(_lib.er_grid_info(self.handle, ctypes.byref(n), ctypes.byref(f), ctypes.byref(e), ctypes.byref(b)),
+               "er_grid_info")
+        return {"n_nodes": n.value, "n_floating": f.value, "n_edges": e.value, "h2d_bytes": b.value}
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            _lib.er_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def grid_create(inst, device: int = -1, stream=None) -> Grid:
+    return Grid(inst, device, stream)
+
+
+def sketch(grid: Grid, k: int, seed: int, prec, Yt, stream=None):
+    return _check(_lib.er_sketch(grid.handle, k, c_uint64(seed), PRECISIONS[prec], _ptr(Yt), _stream(stream)),
+                  "er_sketch")
+
+
+def solve(grid: Grid, Yt, Z, k: int, prec, opts: er_solve_opts | None = None, stream=None, allow_unconverged=False):
+    st = er_solve_stats()
+    ok = (ER_OK, ER_ERR_NOT_CONVERGED) if allow_unconverged else (ER_OK,)
+    s = _lib.er_solve(grid.handle, _ptr(Yt), _ptr(Z), k, PRECISIONS[prec],
+                      ctypes.byref(opts) if opts is not None else None, ctypes.byref(st), _stream(stream))
+    _check(s, "er_solve", ok)
+    return s, st.as_dict()
+
+
+def reff_map(grid: Grid, Z, k: int, prec, R, stream=None):
+    return _check(_lib.er_reff_map(grid.handle, _ptr(Z), k, PRECISIONS[prec], _ptr(R), _stream(stream)),
+                  "er_reff_map")
+
+
+def reff_map_host(inst, k: int, seed: int, prec, opts: er_solve_opts | None = None, R_host=None, stream=None,
+                  allow_unconverged=False):
+    """Host instance in, host R map (numpy FP64) out; copies run inside the library call."""
+    m = _Marshalled(inst)
+    R = np.empty(inst.T * inst.W * inst.H, dtype=np.float64) if R_host is None else R_host
+    st = er_solve_stats()
+    ok = (ER_OK, ER_WARN_FLOATING, ER_ERR_NOT_CONVERGED) if allow_unconverged else (ER_OK, ER_WARN_FLOATING)
+    s = _lib.er_reff_map_host(m.tiers, m.T, m.tsv, m.nt, m.pads, m.npd, k, c_uint64(seed), PRECISIONS[prec],
+                              ctypes.byref(opts) if opts is not None else None,
+                              R.ctypes.data if isinstance(R, np.ndarray) else _ptr(R), ctypes.byref(st),
+                              _stream(stream))
+    _check(s, "er_reff_map_host", ok)
+    return R, st.as_dict()
+
+
+def release_pool():
+    return _lib.er_release_pool()
+
+
+def exported_symbols():
+    return sorted(_sig)
