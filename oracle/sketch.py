@@ -117,7 +117,7 @@ def reff_jl_dense(inst, k, seed, Yt=None):
     Z = np.zeros((n, k))
     Z[keep] = la.cho_solve(la.cho_factor(G, lower=True), Yt[keep])
     R = np.full(n, np.inf)
-    R[keep] = np.sum(Z * Z, axis=1)
+    R[keep] = np.sum(Z[keep] * Z[keep], axis=1)
     return R, Z
 
 

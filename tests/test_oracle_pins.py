@@ -325,3 +325,19 @@ def test_jl_dense_matches_sparse_sampled():
     np.testing.assert_allclose(Zs, Z[nodes], rtol=1e-10, atol=1e-14)
     Rex = exact.reff_dense(inst)
     np.testing.assert_allclose([f.reff(i) for i in nodes], Rex[nodes], rtol=1e-12)
+
+
+def test_jl_with_floating_nodes_matches_sampled():
+    """Floating nodes (no path to a pad) are excluded from the JL route too: R = +inf there
+    and the kept rows equal exact sparse solves."""
+    inst = I.random_small(np.random.default_rng(3), T=1, W=20, H=19, n_pads=1, open_frac=0.35)
+    fl = network.floating_mask(inst)
+    assert fl.any()
+    k, seed = 8, 2
+    Yt = sketch.sketch_numpy(inst, k, seed)
+    R, Z = sketch.reff_jl_dense(inst, k, seed, Yt)
+    assert np.all(np.isinf(R[fl])) and np.all(np.isfinite(R[~fl]))
+    f = exact.SparseFactor(inst)
+    nodes = np.flatnonzero(~fl)[:6]
+    Rs, _ = sketch.reff_jl_sampled(f, Yt, nodes)
+    np.testing.assert_allclose(R[nodes], Rs, rtol=1e-12)
