@@ -93,13 +93,15 @@ typedef struct {
                               (Jacobi-weighted residual; see er_solve) */
     int32_t maxit;         /* iteration cap (both forms, all sweeps together) */
     int32_t check_every;   /* host convergence poll period in iterations (>= 1) */
-    int32_t replace_every; /* ER_FP32_REFINE: FP64 true-residual replacement period m */
-    int32_t max_sweeps;    /* ER_FP32_REFINE: restarts allowed when the FP32 recursion
-                              claims convergence but the FP64 residual disagrees */
+    int32_t replace_every; /* ER_FP32_REFINE: every m iterations the FP32 correction is
+                              folded into the FP64 iterate and the FP64 residual replaces
+                              the recursive one (m >= 1) */
     int32_t use_graph;     /* 1: replay each poll period from a captured CUDA graph */
     int32_t profile;       /* 1: time every pass with CUDA events on the solver's stream
                               (disables graphs); fills er_solve_stats.kernel_ms */
-    int32_t reserved[2];   /* zero */
+    int32_t tile_rows;     /* y rows swept by one CTA (0 = default 64; clipped to H) */
+    int32_t block_order;   /* 0 default, 1 RHS column blocks of a tile adjacent in launch
+                              order, 2 column blocks outermost */
 } er_solve_opts;
 
 /* Pass kinds counted in er_solve_stats.launches / kernel_ms. */
@@ -111,7 +113,7 @@ enum { ER_PASS_A = 0,      /* stencil pass: p' = r + beta p, q = G~ p', dot p'.q
 
 typedef struct {
     int32_t iterations;       /* PCG iterations run */
-    int32_t sweeps;           /* restart sweeps (ER_FP32_REFINE) */
+    int32_t sweeps;           /* FP64 residual replacements (ER_FP32_REFINE) */
     int32_t converged_cols;   /* columns meeting tol at the end */
     int32_t k;
     double max_rel_residual;  /* final FP64 true residual, max over columns, same norm as tol */
@@ -120,8 +122,9 @@ typedef struct {
     double kernel_ms[ER_N_PASS];  /* summed CUDA-event durations by pass kind (profile = 1) */
 } er_solve_stats;
 
-/* Default solve options: tol 1e-12 (FP64) / 1e-6 (FP32), maxit 100000,
- * check_every 10, replace_every 50, max_sweeps 8, use_graph 1, profile 0. */
+/* Default solve options: tol 1e-12 (FP64) / 1e-7 (FP32 form; the FP64 residual of the
+ * FP64 iterate), maxit 20000, check_every 10, replace_every 50, use_graph 1,
+ * profile 0, tile_rows 0, block_order 0. */
 er_solve_opts er_default_solve_opts(er_precision prec);
 
 /* Build the device-resident grid: per-node couplings of the Jacobi-scaled matrix
@@ -155,13 +158,18 @@ er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, voi
                     void *stream);
 
 /* Solve G Z = Yt for k right-hand sides (device arrays [n][k], Z written).
- * Jacobi-preconditioned CG, run as CG on D^-1/2 G D^-1/2 (identical iterates),
- * X0 = 0, each column stopped when its Jacobi-weighted residual meets opts->tol
- * and then frozen.  ER_FP32_REFINE keeps FP32 vectors, accumulates dot products
- * in double-float, recomputes the true residual in FP64 every replace_every
- * iterations and restarts columns whose FP64 residual misses tol.  The library
- * allocates (and caches on the grid) its workspace.  opts/stats may be NULL.
- * Returns ER_ERR_NOT_CONVERGED at maxit (Z valid, stats filled).  Synchronises. */
+ * Jacobi-preconditioned CG from X0 = 0; a column stops when its Jacobi-weighted
+ * residual ||r||_{D^-1} / ||b||_{D^-1} meets opts->tol and is then frozen.
+ * ER_FP64: FP64 throughout (run as CG on D^-1/2 G D^-1/2, identical iterates).
+ * ER_FP32_REFINE: FP32 vectors, stencil and updates on the network with every
+ * conductance rounded to FP32 once (which moves any R by at most a relative 2^-24);
+ * dot products accumulated in FP64; every replace_every iterations the FP32
+ * correction is added to an FP64 iterate and the residual is recomputed in FP64 and
+ * substituted (reliable update, no restart); a column stops only when that FP64
+ * residual meets tol.  Z is written in FP32.  The library allocates (and caches on
+ * the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at
+ * maxit (Z valid, stats filled), ER_ERR_TIMEOUT if a kernel's bounded wait expired.
+ * Synchronises. */
 er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec,
                    const er_solve_opts *opts, er_solve_stats *stats, void *stream);
 

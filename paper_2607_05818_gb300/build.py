@@ -12,7 +12,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = ["er_grid.cu", "er_pcg.cu"]
+SRC = ["er_grid.cu", "er_pcg.cu", "er_fp32.cu"]
 LIB = os.path.join(HERE, "liber.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -36,7 +36,8 @@ def _compile(src: str, obj: str, extra: list[str]) -> str:
 
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     srcs = [os.path.join(HERE, "csrc", s) for s in SRC]
-    hdrs = [os.path.join(HERE, "csrc", "er_internal.h"), os.path.join(ROOT, "include", "er.h")]
+    hdrs = [os.path.join(HERE, "csrc", h) for h in ("er_internal.h", "er_common.cuh")] + [
+        os.path.join(ROOT, "include", "er.h")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in srcs + hdrs + [__file__])
         if os.path.getmtime(LIB) >= newest and not verbose_ptxas:

@@ -28,12 +28,13 @@ er_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? ER_ERR_OOM : ER_ERR_CUDA;
 }
 
-Tiling make_tiling(const GridDev &g, int k, int elem_bytes) {
+Tiling make_tiling(const GridDev &g, int k, int elem_bytes, int rows, int order) {
     Tiling t;
     t.tiles_x = (g.W + kTXI - 1) / kTXI;
     // rows per CTA: long sweeps amortise the two halo rows; short grids use fewer rows
-    int rows = 64;
+    if (rows <= 0) rows = 64;
     if (g.H < rows) rows = g.H;
+    t.cb_fast = order == 2 ? 0 : 1;
     t.rows = rows;
     t.tiles_y = (g.H + rows - 1) / rows;
     t.n_spatial = g.T * t.tiles_y * t.tiles_x;
@@ -210,7 +211,8 @@ bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
 void free_grid_arrays(er::GridDev &d) {
     void *ptrs[] = {d.cE64, d.cS64, d.cE32, d.cS32, d.dinvs, d.tsv_ptr, d.tsv_nbr, d.tsv_c64, d.tsv_c32,
-                    d.gxr, d.gyr, d.tsv_eid, d.tsv_sgn, d.tsv_g, d.pad_ptr, d.pad_eid, d.pad_g, d.floating};
+                    d.gxr, d.gyr, d.tsv_eid, d.tsv_sgn, d.tsv_g, d.pad_ptr, d.pad_eid, d.pad_g, d.floating,
+                    d.coef32, d.tsv_g32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -329,6 +331,39 @@ er_status grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv, 
         pg[ka] = p.g;
     }
     std::vector<float> cE32(cE.begin(), cE.end()), cS32(cS.begin(), cS.end()), tc32(tc.begin(), tc.end());
+    // FP32 form: conductances rounded to FP32 once; the diagonal is summed from the rounded
+    // values in FP64 so the Laplacian rows stay exact; floating nodes get all-zero entries
+    std::vector<float> coef((size_t)n * 4, 0.0f), tg32((size_t)nnz, 0.0f);
+    {
+        std::vector<double> pad_tot((size_t)n, 0.0), d32((size_t)n, 0.0);
+        for (int64_t e = 0; e < n_pads; ++e) {
+            const er_pad &p = pads[e];
+            pad_tot[((int64_t)p.tier * H + p.y) * W + p.x] += p.g;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (floating[i]) continue;
+            const int x = (int)(i % W), y = (int)((i / W) % H);
+            const float ge = x + 1 < W ? (float)gxr[i] : 0.0f, gs = y + 1 < H ? (float)gyr[i] : 0.0f;
+            const float gp = (float)pad_tot[i];
+            coef[4 * i + 1] = ge;
+            coef[4 * i + 2] = gs;
+            coef[4 * i + 3] = gp;
+            d32[i] += (double)ge + (double)gs + (double)gp;
+            if (x + 1 < W) d32[i + 1] += (double)ge;
+            if (y + 1 < H) d32[i + W] += (double)gs;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t e = tcount[i]; e < tcount[i + 1]; ++e) {
+                if (floating[i]) continue;
+                tg32[e] = (float)tg[e];
+                d32[i] += (double)tg32[e];
+            }
+        // 1/d, negated at nodes with TSV segments (a flag the stencil tests instead of the CSR)
+        for (int64_t i = 0; i < n; ++i) {
+            const float dv = floating[i] ? 0.0f : (float)(1.0 / d32[i]);
+            coef[4 * i] = (!floating[i] && tcount[i + 1] > tcount[i]) ? -dv : dv;
+        }
+    }
 
     // all host-side validation is done: now touch the device
     int device = (opt && opt->device >= 0) ? opt->device : -1;
@@ -346,6 +381,7 @@ er_status grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv, 
     UP(tsv_ptr, tcount); UP(tsv_nbr, tnbr); UP(tsv_c64, tc); UP(tsv_c32, tc32);
     UP(gxr, gxr); UP(gyr, gyr); UP(tsv_eid, teid); UP(tsv_sgn, tsgn); UP(tsv_g, tg);
     UP(pad_ptr, pcount); UP(pad_eid, peid); UP(pad_g, pg); UP(floating, floating);
+    UP(coef32, coef); UP(tsv_g32, tg32);
 #undef UP
     if (st == ER_OK) {
         cudaError_t e = cudaStreamSynchronize(stream);

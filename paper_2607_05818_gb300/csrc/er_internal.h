@@ -37,6 +37,7 @@ struct Tiling {
     int n_spatial = 0;   // T * tiles_y * tiles_x
     int kb = 0;          // RHS columns per column block
     int n_colblk = 0;    // ceil(k / kb)
+    int cb_fast = 1;     // launch order: column blocks of a tile adjacent (1) or outermost (0)
     int64_t n_ctas() const { return (int64_t)n_spatial * n_colblk; }
 };
 
@@ -53,6 +54,9 @@ struct GridDev {
     double *cE64 = nullptr, *cS64 = nullptr;
     float *cE32 = nullptr, *cS32 = nullptr;
     double *dinvs = nullptr;  // D^-1/2, 0 at floating nodes
+    // FP32 form: per node {1/d, gE, gS, pad} of the FP32-rounded conductances (edge form)
+    float *coef32 = nullptr;
+    float *tsv_g32 = nullptr;  // per TSV CSR entry
     // TSV adjacency (both directions), CSR over nodes
     int32_t *tsv_ptr = nullptr;  // n + 1
     int32_t *tsv_nbr = nullptr;
@@ -70,7 +74,9 @@ struct GridDev {
     struct Workspace *ws = nullptr;         // cached solve workspace (er_pcg.cu)
 };
 
-Tiling make_tiling(const GridDev &g, int k, int elem_bytes);
+// rows: y rows per CTA (0 = default 64, clipped to H); order: 0 default, 1 column blocks
+// adjacent in launch order, 2 column blocks outermost.
+Tiling make_tiling(const GridDev &g, int k, int elem_bytes, int rows = 0, int order = 0);
 
 // er_pcg.cu
 void free_workspace(GridDev *g);

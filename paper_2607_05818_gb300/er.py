@@ -45,8 +45,8 @@ class er_options(ctypes.Structure):
 
 class er_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("check_every", c_int32),
-                ("replace_every", c_int32), ("max_sweeps", c_int32), ("use_graph", c_int32),
-                ("profile", c_int32), ("reserved", c_int32 * 2)]
+                ("replace_every", c_int32), ("use_graph", c_int32),
+                ("profile", c_int32), ("tile_rows", c_int32), ("block_order", c_int32)]
 
 
 class er_solve_stats(ctypes.Structure):

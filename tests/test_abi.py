@@ -48,7 +48,7 @@ int main(void) {
   printf("er_tsv %zu %zu\n", sizeof(er_tsv), offsetof(er_tsv, g));
   printf("er_pad %zu %zu\n", sizeof(er_pad), offsetof(er_pad, g));
   printf("er_options %zu\n", sizeof(er_options));
-  printf("er_solve_opts %zu %zu %zu %zu\n", sizeof(er_solve_opts), offsetof(er_solve_opts, maxit), offsetof(er_solve_opts, use_graph), offsetof(er_solve_opts, profile));
+  printf("er_solve_opts %zu %zu %zu %zu %zu\n", sizeof(er_solve_opts), offsetof(er_solve_opts, maxit), offsetof(er_solve_opts, use_graph), offsetof(er_solve_opts, profile), offsetof(er_solve_opts, block_order));
   printf("er_solve_stats %zu %zu %zu %zu %zu\n", sizeof(er_solve_stats), offsetof(er_solve_stats, max_rel_residual), offsetof(er_solve_stats, seconds), offsetof(er_solve_stats, launches), offsetof(er_solve_stats, kernel_ms));
   return 0;
 }
@@ -62,7 +62,8 @@ int main(void) {
     assert out["er_pad"] == [S(er.er_pad), er.er_pad.g.offset]
     assert out["er_options"] == [S(er.er_options)]
     assert out["er_solve_opts"] == [S(er.er_solve_opts), er.er_solve_opts.maxit.offset,
-                                    er.er_solve_opts.use_graph.offset, er.er_solve_opts.profile.offset]
+                                    er.er_solve_opts.use_graph.offset, er.er_solve_opts.profile.offset,
+                                    er.er_solve_opts.block_order.offset]
     assert out["er_solve_stats"] == [S(er.er_solve_stats), er.er_solve_stats.max_rel_residual.offset,
                                      er.er_solve_stats.seconds.offset, er.er_solve_stats.launches.offset,
                                      er.er_solve_stats.kernel_ms.offset]
@@ -71,7 +72,7 @@ int main(void) {
 def test_default_options(er):
     o64 = er.default_solve_opts("fp64")
     o32 = er.default_solve_opts("fp32")
-    assert o64.tol == 1e-12 and o32.tol == 1e-6
+    assert o64.tol == 1e-12 and o32.tol == 1e-7
     assert o64.maxit > 0 and o64.check_every >= 1 and o32.replace_every == 50
 
 
