@@ -173,6 +173,23 @@ er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, voi
 er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec,
                    const er_solve_opts *opts, er_solve_stats *stats, void *stream);
 
+/* The FP64 form of er_solve without any device allocation, for callers that cannot
+ * allocate device memory at solve time: code that runs under an allocator that forbids
+ * device allocation after start-up, memory-capped serving processes that must not grow,
+ * or loops that cannot accept the implicit synchronisation of cudaMalloc/cudaFree.
+ * (The paper has no counterpart: this is a deployment variant of the solve.)
+ * The solver workspace lives in one file-scope device array of about 9.1 MB, held by
+ * every GPU that loads the library until the process exits; sizes are limited to
+ * n*k <= 262144 and k <= 4096, and larger requests return ER_ERR_INVALID_ARG.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) and should
+ * come before any stream capture.  All calls share the array: each call clears the
+ * counters and flags it needs, runs on `stream` without graphs or event timing, and
+ * returns when done; calls are serialised by a process-wide lock, and calls that overlap
+ * on the GPU would race.  Yt and Z are FP64 [n][k] device arrays as for er_solve; the
+ * grid must have been created beforehand.  Same statuses as er_solve. */
+er_status er_solve_noalloc(er_grid *g, const void *Yt, void *Z, int32_t k, const er_solve_opts *opts,
+                           er_solve_stats *stats, void *stream);
+
 /* R_i = sum_j Z_ij^2 into device array R [n] (FP64); +inf for floating nodes.
  * Z is FP64 or FP32 per `prec`.  Async on `stream`. */
 er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R,

@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 
+#include <chrono>
 #include <vector>
 
 #include "er_internal.h"
@@ -225,7 +226,8 @@ struct Workspace {
     double *part = nullptr, *scal = nullptr;  // scal: alpha, beta, rho, rho0, resid (k each)
     int *ints = nullptr;                      // active[k], col_active[n_colblk], err
     unsigned *counter = nullptr;
-    int *h_poll = nullptr;                    // pinned: col_active + err
+    int *h_poll = nullptr;                    // host: col_active + err (pinned in the cached workspace)
+    double *h_resid = nullptr;                // host: k final residuals
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -266,6 +268,11 @@ struct Prof {
 
 void prof_begin(Workspace &w, Prof *pf, int kind);
 void prof_end(Workspace &w, Prof *pf, int kind);
+
+// er_pcg.cu: argument checks and the solve loop on a prepared workspace
+er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts &opt);
+er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er_precision prec,
+                     const er_solve_opts &opt, er_solve_stats *stats, std::chrono::steady_clock::time_point t0);
 
 // er_fp32.cu: the FP32 form's passes (all asynchronous on w.s)
 er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z);

@@ -418,38 +418,57 @@ static er_status poll(Workspace &w, Prof &pf, int *n_active, int *err) {
 //  replace_every iterations (and whenever every column's recursive residual meets tol)
 //  the FP32 correction is folded into the FP64 iterate and the FP64 residual replaces
 //  the recursive one; a column stops only when that FP64 residual meets tol.
-er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts *o,
-                er_solve_stats *stats, cudaStream_t us) {
-    auto t0 = std::chrono::steady_clock::now();
-    if (!gg) return fail(ER_ERR_INVALID_ARG, "grid is NULL");
+er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts &opt) {
     if (k < 4 || (k & 3)) return fail(ER_ERR_INVALID_ARG, "k must be a positive multiple of 4");
     if (!Yt || !Z) return fail(ER_ERR_INVALID_ARG, "Yt or Z is NULL");
     if (((uintptr_t)Yt & 15u) || ((uintptr_t)Z & 15u)) return fail(ER_ERR_INVALID_ARG, "Yt and Z must be 16-byte aligned");
     if (Yt == Z) return fail(ER_ERR_INVALID_ARG, "Yt and Z must not alias");
     if (prec != ER_FP64 && prec != ER_FP32_REFINE) return fail(ER_ERR_INVALID_ARG, "bad precision");
-    er_solve_opts opt = o ? *o : er_default_solve_opts(prec);
     if (!(opt.tol > 0.0) || opt.maxit < 1 || opt.check_every < 1 || opt.replace_every < 1)
         return fail(ER_ERR_INVALID_ARG, "bad solve options");
     if (opt.tile_rows < 0 || opt.block_order < 0 || opt.block_order > 2)
         return fail(ER_ERR_INVALID_ARG, "bad tile options");
+    return ER_OK;
+}
+
+er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts *o,
+                er_solve_stats *stats, cudaStream_t us) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!gg) return fail(ER_ERR_INVALID_ARG, "grid is NULL");
+    er_solve_opts opt = o ? *o : er_default_solve_opts(prec);
+    er_status st = check_solve_args(Yt, Z, k, prec, opt);
+    if (st != ER_OK) return st;
     std::lock_guard<std::mutex> lock(gg->mu);
     GridDev &g = gg->d;
     ER_CUDA(cudaSetDevice(g.device));
     Workspace *wp = nullptr;
-    er_status st = get_workspace(&g, k, prec, opt.tile_rows, opt.block_order, &wp);
+    st = get_workspace(&g, k, prec, opt.tile_rows, opt.block_order, &wp);
     if (st != ER_OK) {
         free_workspace(&g);
         return st;
     }
     Workspace &w = *wp;
-    const bool fp32 = prec == ER_FP32_REFINE;
-    const double tol = opt.tol;
-    if (fp32) {
+    if (prec == ER_FP32_REFINE) {
         st = fp32_prepare(g, w, Yt, Z);
         if (st != ER_OK) return st;
     }
     ER_CUDA(cudaEventRecord(w.ev, us));
     ER_CUDA(cudaStreamWaitEvent(w.s, w.ev, 0));
+    std::vector<double> resid((size_t)k);
+    w.h_resid = resid.data();
+    st = solve_core(g, w, Yt, Z, prec, opt, stats, t0);
+    w.h_resid = nullptr;
+    return st;
+}
+
+// The solve loop on a prepared workspace (stream w.s, poll buffer w.h_poll).  Launches
+// kernels and copies only; graphs and event timing only when opt asks for them.
+er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er_precision prec,
+                     const er_solve_opts &opt, er_solve_stats *stats, std::chrono::steady_clock::time_point t0) {
+    const int k = w.k;
+    er_status st = ER_OK;
+    const bool fp32 = prec == ER_FP32_REFINE;
+    const double tol = opt.tol;
     ER_CUDA(cudaMemsetAsync(w.ints + w.k + w.til.n_colblk, 0, sizeof(int), w.s));
     Prof pf;
     pf.on = opt.profile != 0;
@@ -535,17 +554,17 @@ er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision pr
         launch(k_stream<double, MODE_UNSCALE>, a, w, &pf, ER_PASS_OTHER);
     }
     ER_CUDA(cudaGetLastError());
-    std::vector<double> resid((size_t)k);
-    ER_CUDA(cudaMemcpyAsync(resid.data(), w.scal + 4 * k, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, w.s));
+    double *resid = w.h_resid;
+    ER_CUDA(cudaMemcpyAsync(resid, w.scal + 4 * k, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, w.s));
     ER_CUDA(cudaMemcpyAsync(w.h_poll, w.ints + w.k + w.til.n_colblk, sizeof(int), cudaMemcpyDeviceToHost, w.s));
     ER_CUDA(cudaStreamSynchronize(w.s));
     flush_prof(w, pf);
     err |= w.h_poll[0];
     int ok_cols = 0;
     double mx = 0.0;
-    for (double r : resid) {
-        mx = std::max(mx, r);
-        ok_cols += (r <= tol);
+    for (int j = 0; j < k; ++j) {
+        mx = std::max(mx, resid[j]);
+        ok_cols += (resid[j] <= tol);
     }
     if (stats) {
         stats->iterations = it;

@@ -74,6 +74,8 @@ _sig = {
     "er_sketch": (_S, [c_void_p, c_int32, c_uint64, c_int32, c_void_p, c_void_p]),
     "er_solve": (_S, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(er_solve_opts),
                       POINTER(er_solve_stats), c_void_p]),
+    "er_solve_noalloc": (_S, [c_void_p, c_void_p, c_void_p, c_int32, POINTER(er_solve_opts),
+                              POINTER(er_solve_stats), c_void_p]),
     "er_reff_map": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "er_reff_map_host": (_S, [POINTER(er_tier), c_int32, POINTER(er_tsv), c_int64, POINTER(er_pad), c_int64,
                               c_int32, c_uint64, c_int32, POINTER(er_solve_opts), c_void_p,
@@ -211,6 +213,17 @@ def solve(grid: Grid, Yt, Z, k: int, prec, opts: er_solve_opts | None = None, st
     s = _lib.er_solve(grid.handle, _ptr(Yt), _ptr(Z), k, PRECISIONS[prec],
                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(st), _stream(stream))
     _check(s, "er_solve", ok)
+    return s, st.as_dict()
+
+
+def solve_noalloc(grid: Grid, Yt, Z, k: int, opts: er_solve_opts | None = None, stream=None,
+                  allow_unconverged=False):
+    """FP64 solve whose workspace is a fixed static device array (no device allocation)."""
+    st = er_solve_stats()
+    ok = (ER_OK, ER_ERR_NOT_CONVERGED) if allow_unconverged else (ER_OK,)
+    s = _lib.er_solve_noalloc(grid.handle, _ptr(Yt), _ptr(Z), k,
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(st), _stream(stream))
+    _check(s, "er_solve_noalloc", ok)
     return s, st.as_dict()
 
 
