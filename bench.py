@@ -239,25 +239,30 @@ def run_ours(args, rank, world, local_rank):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_note = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
     nk = inst.n * k
-    coef = 16 * inst.n  # cE, cS and two TSV row pointers per node
-    per = {  # algorithmic bytes per launch of each pass
-        "A": (2 * nk * es + coef) if prec == "fp32" else (4 * nk * es + coef),
-        "B": (6 * nk * es + coef) if prec == "fp32" else (6 * nk * es),
-    }
-    names = {"A": "k_tma<MODE_A_DOT>" if prec == "fp32" else "k_stencil<double,double,MODE_A_STORE>",
-             "B": "k_tma<MODE_B>" if prec == "fp32" else "k_stream<double,MODE_S>"}
+    coef = 16 * inst.n  # per-node coefficient words read by a stencil pass
+    if prec == "fp32":
+        # (pass kind index, kernel, algorithmic bytes per launch)
+        kinds = [(1, "k_tma<MODE_B>", 6 * nk * es + coef),   # odd iterations: r, p, x in; x, r, p' out
+                 (4, "k_tma<MODE_B0>", 4 * nk * es + coef),  # even iterations: r, p in; r, p' out
+                 (0, "k_tma<MODE_A_DOT>", 2 * nk * es + coef)]  # r, p in
+    else:
+        kinds = [(0, "k_stencil<double,double,MODE_A_STORE>", 4 * nk * es + coef),
+                 (1, "k_stream<double,MODE_S>", 6 * nk * es)]
     rl = []
-    for key, idx in (("B", 1), ("A", 0)):
+    for idx, name, nbytes in kinds:
         n_l = int(launches[idx])
         avg_ms = float(kms[idx]) / max(n_l, 1)
-        ach = per[key] / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
-        rl.append({"kernel": names[key], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                   "frac": (ach / peak) if ach else None, "traffic": ncu_traffic(names[key], args.workload),
-                   "algorithmic_bytes_per_launch": per[key], "avg_launch_ms": avg_ms, "launches": n_l,
+        ach = nbytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
+        rl.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                   "frac": (ach / peak) if ach else None, "traffic": ncu_traffic(name, args.workload),
+                   "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms, "launches": n_l,
                    "share_of_step": float(kms[idx]) / ms if ms > 0 else None, "peak_source": peak_note})
+    rl.sort(key=lambda r: -(r["share_of_step"] or 0))
+    pass_names = ["A", "B", "R", "other", "B0"]
+    pass_ms_per_step = {pass_names[i]: float(kms[i]) / args.steps for i in range(len(kms))}
     gpu_launches = int(launches.sum()) + 2 * args.steps  # + sketch and reff_map per step
 
-    result = {"rank0_iterations": iters, "stats_last": stats[-1],
+    result = {"rank0_iterations": iters, "stats_last": stats[-1], "pass_ms_per_step": pass_ms_per_step,
               "replacements": [s["sweeps"] for s in stats],
               "max_rel_residual": max(s["max_rel_residual"] for s in stats)}
     acc = None
@@ -356,7 +361,8 @@ def main():
                        "iterations_per_step": result["rank0_iterations"],
                        "fp64_residual_replacements_per_step": result["replacements"],
                        "tol": args.tol if args.tol is not None else ("1e-7" if args.prec == "fp32" else "1e-12"),
-                       "final_max_rel_residual": result["max_rel_residual"]},
+                       "final_max_rel_residual": result["max_rel_residual"],
+                       "kernel_ms_per_step_by_pass": result["pass_ms_per_step"]},
             "roofline": rl[0], "roofline_other": rl[1:], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "accuracy": acc,
         }

@@ -105,11 +105,13 @@ typedef struct {
 } er_solve_opts;
 
 /* Pass kinds counted in er_solve_stats.launches / kernel_ms. */
-enum { ER_PASS_A = 0,      /* stencil pass: p' = r + beta p, q = G~ p', dot p'.q */
-       ER_PASS_B = 1,      /* update pass: x, r (and p' in the FP32 form), dot r.r */
-       ER_PASS_R = 2,      /* FP64 true-residual pass */
-       ER_PASS_OTHER = 3,  /* initialisation and final unscaling */
-       ER_N_PASS = 4 };
+enum { ER_PASS_A = 0,      /* stencil pass: p' = z + beta p, q = G p', dot p'.q */
+       ER_PASS_B = 1,      /* update pass: x, r (and p' in the FP32 form), dot r.z; in the
+                              FP32 form the odd iterations, which also update x */
+       ER_PASS_R = 2,      /* FP64 residual pass */
+       ER_PASS_OTHER = 3,  /* initialisation, FP64 accumulation of x, final Z */
+       ER_PASS_B0 = 4,     /* FP32 form, even iterations: update pass without x */
+       ER_N_PASS = 5 };
 
 typedef struct {
     int32_t iterations;       /* PCG iterations run */

@@ -19,7 +19,9 @@ enum Mode {
     MODE_S = 4,        // streaming x += alpha p', r -= alpha q; dot r.r
     MODE_INIT = 5,     // r = b (scaled in the FP64 form), x = 0, p = 0; dot r.z
     MODE_UNSCALE = 6,  // final Z from the iterate
-    MODE_ACCUM = 7     // FP32 form: x64 += x, x = 0
+    MODE_ACCUM = 7,    // FP32 form: x64 += x, x = 0
+    MODE_B0 = 8        // FP32 form, even iterations: as B without touching x (x is updated
+                       // with two iterations' steps in the following odd one)
 };
 
 // Arguments of every node-by-RHS kernel.  T: storage type of the [n][k] vectors,
@@ -36,7 +38,7 @@ struct KArgs {
     const float *tsv_g32;               // FP32 form: TSV conductance per CSR entry
     const int32_t *tsv_ptr, *tsv_nbr;
     const double *dinvs;                // FP64 form: D^-1/2
-    double *alpha, *beta, *rho, *rho0, *resid;
+    double *alpha, *beta, *rho, *rho0, *resid, *alpha_prev;
     int *active, *col_active, *err;
     unsigned *counter;
     double *part;
@@ -102,13 +104,14 @@ __device__ inline void stv(T *p, const C (&v)[V]) {
 template <typename T, typename C, int MODE>
 __device__ inline void finalize_column(const KArgs<T, C> &a, int j, double total, int &nact) {
     if constexpr (MODE == MODE_A_DOT || MODE == MODE_A_STORE) {
+        a.alpha_prev[j] = a.alpha[j];
         if (a.active[j] && total > 0.0 && isfinite(total)) {
             a.alpha[j] = a.rho[j] / total;
         } else {
             a.alpha[j] = 0.0;
             a.active[j] = 0;
         }
-    } else if constexpr (MODE == MODE_B || MODE == MODE_S) {
+    } else if constexpr (MODE == MODE_B || MODE == MODE_B0 || MODE == MODE_S) {
         if (a.active[j]) {
             const double rho = a.rho[j];
             a.beta[j] = rho > 0.0 ? total / rho : 0.0;
@@ -144,6 +147,7 @@ __device__ inline void finalize_column(const KArgs<T, C> &a, int j, double total
         a.rho0[j] = total;
         a.rho[j] = total;
         a.alpha[j] = 0.0;
+        a.alpha_prev[j] = 0.0;
         a.beta[j] = 0.0;
         a.active[j] = total > 0.0 ? 1 : 0;
         a.resid[j] = total > 0.0 ? 1.0 : 0.0;
@@ -223,7 +227,7 @@ struct Workspace {
     Tiling til;
     void *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr}, *q = nullptr;
     double *x64 = nullptr;                    // FP32 form: FP64 iterate
-    double *part = nullptr, *scal = nullptr;  // scal: alpha, beta, rho, rho0, resid (k each)
+    double *part = nullptr, *scal = nullptr;  // scal: alpha, beta, rho, rho0, resid, alpha_prev (k each)
     int *ints = nullptr;                      // active[k], col_active[n_colblk], err
     unsigned *counter = nullptr;
     int *h_poll = nullptr;                    // host: col_active + err (pinned in the cached workspace)
@@ -250,7 +254,7 @@ KArgs<T, C> base_args(const GridDev &g, const Workspace &w, double tol) {
     a.tsv_ptr = g.tsv_ptr; a.tsv_nbr = g.tsv_nbr; a.dinvs = g.dinvs;
     a.coef = reinterpret_cast<const float4 *>(g.coef32); a.tsv_g32 = g.tsv_g32;
     a.alpha = w.scal; a.beta = w.scal + w.k; a.rho = w.scal + 2 * w.k; a.rho0 = w.scal + 3 * w.k;
-    a.resid = w.scal + 4 * w.k;
+    a.resid = w.scal + 4 * w.k; a.alpha_prev = w.scal + 5 * w.k;
     a.active = w.ints; a.col_active = w.ints + w.k; a.err = w.ints + w.k + w.til.n_colblk;
     a.counter = w.counter; a.part = w.part; a.tol = tol;
     return a;
@@ -260,8 +264,8 @@ KArgs<T, C> base_args(const GridDev &g, const Workspace &w, double tol) {
 // the solver stream (read back at the next host poll).
 struct Prof {
     bool on = false;
-    int launches[ER_N_PASS] = {0, 0, 0, 0};
-    double ms[ER_N_PASS] = {0.0, 0.0, 0.0, 0.0};
+    int launches[ER_N_PASS] = {};
+    double ms[ER_N_PASS] = {};
     size_t used = 0;
     std::vector<int> kinds;
 };

@@ -89,8 +89,12 @@ struct Layout<MODE_A_DOT> {  // stage: r, p, coef
     static constexpr int NS = 5, OFF_R = 0, OFF_P = 4096, OFF_X = -1, OFF_COEF = 8192, BYTES = 8704;
 };
 template <>
-struct Layout<MODE_B> {  // stage: r, p, x, coef
+struct Layout<MODE_B> {  // odd iterations; stage: r, p, x, coef
     static constexpr int NS = 4, OFF_R = 0, OFF_P = 4096, OFF_X = 8192, OFF_COEF = 12288, BYTES = 12800;
+};
+template <>
+struct Layout<MODE_B0> {  // even iterations; stage: r, p, coef
+    static constexpr int NS = 4, OFF_R = 0, OFF_P = 4096, OFF_X = -1, OFF_COEF = 8192, BYTES = 8704;
 };
 template <>
 struct Layout<MODE_R> {  // stage: x64 (FP64), b, coef
@@ -104,6 +108,9 @@ template <int MODE>
 constexpr int dyn_smem() { return Layout<MODE>::NS * Layout<MODE>::BYTES + ring_bytes<MODE>() + 128; }
 
 __device__ __forceinline__ float4 lds4(const unsigned char *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// component v of a float4 (v is a compile-time constant after unrolling)
+__device__ __forceinline__ float f4(const float4 &f, int v) { return v == 0 ? f.x : v == 1 ? f.y : v == 2 ? f.z : f.w; }
 
 // One pass over a CTA's tile.  Step ri (row y = y0 - 1 + ri) waits for its stage, reads the
 // thread's own node from it into registers (r, p or x64, x, coefficients), forms the
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
     Cv *ring = reinterpret_cast<Cv *>(smem + L::NS * L::BYTES);  // [2][kNX][KB]
     __shared__ __align__(8) uint64_t bars[L::NS];
     __shared__ int s_abort;
-    __shared__ __align__(16) float s_beta[KB], s_alpha[KB];  // per-column CG scalars
+    __shared__ __align__(16) float s_beta[KB], s_alpha[KB], s_alpha_prev[KB];  // per-column CG scalars
     const KArgs<float, float> &a = ta.a;
 
     const int lc = threadIdx.x % kTPN, xl = threadIdx.x / kTPN;
@@ -146,7 +153,8 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
     if (threadIdx.x < KB) {
         const int j = c0 + threadIdx.x;
         s_beta[threadIdx.x] = (j < a.k && !R64) ? (float)a.beta[j] : 0.f;
-        s_alpha[threadIdx.x] = (j < a.k && MODE == MODE_B) ? (float)a.alpha[j] : 0.f;
+        s_alpha[threadIdx.x] = (j < a.k && (MODE == MODE_B || MODE == MODE_B0)) ? (float)a.alpha[j] : 0.f;
+        s_alpha_prev[threadIdx.x] = (j < a.k && MODE == MODE_B) ? (float)a.alpha_prev[j] : 0.f;
     }
     __syncthreads();
 
@@ -191,21 +199,21 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
 
     // registers: operand at rows y-2 (vn), y-1 (vc); r/x/b and coefficients of row y-1
     Cv vn[V], vc[V];
-    float rc[V], xc[V];
+    float rc[V];
     float4 cfc = make_float4(0.f, 0.f, 0.f, 0.f);  // {+-1/d, gE, gS, pad} of row y-1, own node
     float gwc = 0.f, gsn = 0.f;                    // gE of the west node (row y-1); gS of row y-2
     float run[V] = {0.f, 0.f, 0.f, 0.f};
     double acc[V] = {0.0, 0.0, 0.0, 0.0};
     int nrun = 0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) vn[v] = vc[v] = (Cv)0, rc[v] = xc[v] = 0.f;
+    for (int v = 0; v < V; ++v) vn[v] = vc[v] = (Cv)0, rc[v] = 0.f;
 
     for (int ri = 0; ri < nrow; ++ri) {
         wait_row(ri);
         const unsigned char *st = smem + (ri % L::NS) * L::BYTES;
         // own node of row ri from the stage
         Cv vs[V];
-        float rs[V], xs[V];
+        float rs[V], xs[V], ps[V];
         const float4 cfs = lds4(st + L::OFF_COEF + xl * 16);
         const float gws = xl > 0 ? lds4(st + L::OFF_COEF + (xl - 1) * 16).y : 0.f;
         if constexpr (R64) {
@@ -221,6 +229,7 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
             const float4 r = lds4(st + L::OFF_R + xl * 128 + lc * 16);
             const float4 p = lds4(st + L::OFF_P + xl * 128 + lc * 16);
             rs[0] = r.x; rs[1] = r.y; rs[2] = r.z; rs[3] = r.w;
+            ps[0] = p.x; ps[1] = p.y; ps[2] = p.z; ps[3] = p.w;
             vs[0] = fmaf(be[0], p.x, dinv * r.x);
             vs[1] = fmaf(be[1], p.y, dinv * r.y);
             vs[2] = fmaf(be[2], p.z, dinv * r.z);
@@ -228,6 +237,21 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
             if constexpr (MODE == MODE_B) {
                 const float4 xx = lds4(st + L::OFF_X + xl * 128 + lc * 16);
                 xs[0] = xx.x; xs[1] = xx.y; xs[2] = xx.z; xs[3] = xx.w;
+            }
+        }
+        // pass B: p' and (odd iterations) x of row ri need no neighbour: write them now
+        if constexpr (MODE == MODE_B || MODE == MODE_B0) {
+            if (own && ri >= 1 && ri + 1 < nrow) {
+                const int64_t idx = (tbase + (int64_t)(y0 - 1 + ri) * a.W + x) * a.k + col;
+                stv<float, float, V>(a.p_out + idx, vs);
+                if constexpr (MODE == MODE_B) {  // x += alpha_prev p_prev + alpha p'
+                    const float4 a4 = *reinterpret_cast<const float4 *>(s_alpha + lc * V);
+                    const float4 b4 = *reinterpret_cast<const float4 *>(s_alpha_prev + lc * V);
+                    float xn[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) xn[v] = fmaf(f4(a4, v), vs[v], fmaf(f4(b4, v), ps[v], xs[v]));
+                    stv<float, float, V>(a.x + idx, xn);
+                }
             }
         }
         // row y-1: q = pad v + gE (v - v_e) + gW (v - v_w) + gS (v - v_s) + gN (v - v_n) + TSVs
@@ -249,39 +273,71 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
                 ve[0] = e4.x; ve[1] = e4.y; ve[2] = e4.z; ve[3] = e4.w;
             }
             const Cv gp = cfc.w, ge = cfc.y, gs = cfc.z, gw = gwc, gn = gsn;
+            if constexpr (MODE == MODE_A_DOT) {
+                // p'.Gp' as a sum over edges: pad p^2 + gE (p - pE)^2 + gS (p - pS)^2 at each node,
+                // plus half of every TSV segment at each of its two ends
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                Cv qq = gp * vc[v];
-                qq = fma(ge, vc[v] - ve[v], qq);
-                qq = fma(gw, vc[v] - vw[v], qq);
-                qq = fma(gs, vc[v] - vs[v], qq);
-                qq = fma(gn, vc[v] - vn[v], qq);
-                q[v] = qq;
+                for (int v = 0; v < V; ++v) {
+                    const float de = vc[v] - ve[v], ds = vc[v] - vs[v];
+                    float e = gp * vc[v] * vc[v];
+                    e = fmaf(ge * de, de, e);
+                    e = fmaf(gs * ds, ds, e);
+                    q[v] = e;
+                }
+            } else if constexpr (R64) {
+                // diagonal form: d v - sum_j g_j v_j, d summed exactly in FP64 from the FP32 g's
+                Cv d = gp + ge + gw + gs + gn;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    Cv qq = -ge * ve[v];
+                    qq = fma(-gw, vw[v], qq);
+                    qq = fma(-gs, vs[v], qq);
+                    qq = fma(-gn, vn[v], qq);
+                    q[v] = qq;
+                }
+                if (cfc.x < 0.f) {
+                    const int e1 = a.tsv_ptr[i + 1];
+                    for (int e = a.tsv_ptr[i]; e < e1; ++e) {
+                        const int64_t jdx = (int64_t)a.tsv_nbr[e] * a.k + col;
+                        const double g = a.tsv_g32[e];
+                        const double2 lo = *reinterpret_cast<const double2 *>(a.x64 + jdx);
+                        const double2 hi = *reinterpret_cast<const double2 *>(a.x64 + jdx + 2);
+                        d += g;
+                        q[0] = fma(-g, lo.x, q[0]);
+                        q[1] = fma(-g, lo.y, q[1]);
+                        q[2] = fma(-g, hi.x, q[2]);
+                        q[3] = fma(-g, hi.y, q[3]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) q[v] = fma(d, vc[v], q[v]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    Cv qq = gp * vc[v];
+                    qq = fma(ge, vc[v] - ve[v], qq);
+                    qq = fma(gw, vc[v] - vw[v], qq);
+                    qq = fma(gs, vc[v] - vs[v], qq);
+                    qq = fma(gn, vc[v] - vn[v], qq);
+                    q[v] = qq;
+                }
             }
-            if (cfc.x < 0.f) {  // node with TSV segments
+            if (!R64 && cfc.x < 0.f) {  // node with TSV segments (FP32 passes)
                 const int e1 = a.tsv_ptr[i + 1];
                 for (int e = a.tsv_ptr[i]; e < e1; ++e) {
                     const int j = a.tsv_nbr[e];
                     const int64_t jdx = (int64_t)j * a.k + col;
-                    const Cv g = a.tsv_g32[e];
-                    Cv vj[V];
-                    if constexpr (R64) {
-                        const double2 lo = *reinterpret_cast<const double2 *>(a.x64 + jdx);
-                        const double2 hi = *reinterpret_cast<const double2 *>(a.x64 + jdx + 2);
-                        vj[0] = lo.x; vj[1] = lo.y; vj[2] = hi.x; vj[3] = hi.y;
-                    } else {
-                        float be[V];
-                        load_be(be);
-                        const float dj = fabsf(a.coef[j].x);
-                        const float4 rj = *reinterpret_cast<const float4 *>(a.r_in + jdx);
-                        const float4 pj = *reinterpret_cast<const float4 *>(a.p_in + jdx);
-                        vj[0] = fmaf(be[0], pj.x, dj * rj.x);
-                        vj[1] = fmaf(be[1], pj.y, dj * rj.y);
-                        vj[2] = fmaf(be[2], pj.z, dj * rj.z);
-                        vj[3] = fmaf(be[3], pj.w, dj * rj.w);
-                    }
+                    const float g = a.tsv_g32[e];
+                    const float4 b4 = *reinterpret_cast<const float4 *>(s_beta + lc * V);
+                    const float dj = fabsf(a.coef[j].x);
+                    const float4 rj = *reinterpret_cast<const float4 *>(a.r_in + jdx);
+                    const float4 pj = *reinterpret_cast<const float4 *>(a.p_in + jdx);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) q[v] = fma(g, vc[v] - vj[v], q[v]);
+                    for (int v = 0; v < V; ++v) {
+                        const float dv = (float)vc[v] - fmaf(f4(b4, v), f4(pj, v), dj * f4(rj, v));
+                        if constexpr (MODE == MODE_A_DOT) q[v] = fmaf(0.5f * g * dv, dv, (float)q[v]);
+                        else q[v] = fmaf(g, dv, (float)q[v]);
+                    }
                 }
             }
             if constexpr (R64) {
@@ -296,21 +352,17 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
                 stv<float, float, V>(a.r_out + idx, ro);
             } else if constexpr (MODE == MODE_A_DOT) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) run[v] = fmaf(vc[v], q[v], run[v]);
+                for (int v = 0; v < V; ++v) run[v] += q[v];
             } else {
                 const float dinv = fabsf(cfc.x);
                 const float4 a4 = *reinterpret_cast<const float4 *>(s_alpha + lc * V);
-                const float al[V] = {a4.x, a4.y, a4.z, a4.w};
-                float xn[V], rn[V];
+                float rn[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    xn[v] = fmaf(al[v], vc[v], xc[v]);
-                    rn[v] = fmaf(-al[v], q[v], rc[v]);
+                    rn[v] = fmaf(-f4(a4, v), q[v], rc[v]);
                     run[v] = fmaf(dinv * rn[v], rn[v], run[v]);
                 }
-                stv<float, float, V>(a.x + idx, xn);
                 stv<float, float, V>(a.r_out + idx, rn);
-                stv<float, float, V>(a.p_out + idx, vc);
             }
             if constexpr (!R64) {
                 if (++nrun == 8) {
@@ -341,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
             vn[v] = vc[v];
             vc[v] = vs[v];
             rc[v] = rs[v];
-            if constexpr (MODE == MODE_B) xc[v] = xs[v];
+
         }
         __syncthreads();
         if (threadIdx.x == 0 && ri + L::NS < nrow && !s_abort) issue(ri + L::NS);
@@ -483,6 +535,8 @@ er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z) 
                                      dyn_smem<MODE_A_DOT>()));
         ER_CUDA(cudaFuncSetAttribute(k_tma<MODE_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_B>()));
+        ER_CUDA(cudaFuncSetAttribute(k_tma<MODE_B0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dyn_smem<MODE_B0>()));
         ER_CUDA(cudaFuncSetAttribute(k_tma<MODE_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_R>()));
         g_attr_done = true;
@@ -528,8 +582,12 @@ int fp32_iterate(const GridDev &g, Workspace &w, void *Z, double tol, int cur, P
     ta.a.r_out = (float *)w.r[1 - cur];
     ta.a.p_out = (float *)w.p[1 - cur];
     ta.a.freeze = 0;
-    ta.tm[2] = w.tm_c;
-    launch_tma<MODE_B>(ta, w, pf, ER_PASS_B);
+    if (cur == 1) {  // odd iteration: x gains this and the previous iteration's steps
+        ta.tm[2] = w.tm_c;
+        launch_tma<MODE_B>(ta, w, pf, ER_PASS_B);
+    } else {
+        launch_tma<MODE_B0>(ta, w, pf, ER_PASS_B0);
+    }
     return 1 - cur;
 }
 

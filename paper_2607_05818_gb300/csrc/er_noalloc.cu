@@ -23,7 +23,7 @@ constexpr int kNaMaxColblk = 512;
 constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kNaVec = na_round(kNaMaxElems * sizeof(double));
 constexpr size_t kNaPart = na_round(kNaMaxPartials * sizeof(double));
-constexpr size_t kNaScal = na_round(5 * (size_t)kNaMaxK * sizeof(double));
+constexpr size_t kNaScal = na_round(6 * (size_t)kNaMaxK * sizeof(double));
 constexpr size_t kNaInts = na_round(((size_t)kNaMaxK + kNaMaxColblk + 1) * sizeof(int));
 constexpr size_t kNaCnt = na_round((size_t)kNaMaxColblk * sizeof(unsigned));
 constexpr size_t kNaBytes = 4 * kNaVec + kNaPart + kNaScal + kNaInts + kNaCnt;  // about 9.1 MB

@@ -317,7 +317,7 @@ static er_status get_workspace(GridDev *g, int k, er_precision prec, int rows, i
         ER_CUDA(cudaMalloc((void **)&w->x64, (size_t)g->n * (size_t)k * sizeof(double)));
     }
     ER_CUDA(cudaMalloc(&w->part, (size_t)w->til.n_spatial * k * sizeof(double)));
-    ER_CUDA(cudaMalloc(&w->scal, (size_t)5 * k * sizeof(double)));
+    ER_CUDA(cudaMalloc(&w->scal, (size_t)6 * k * sizeof(double)));
     const size_t nint = (size_t)k + w->til.n_colblk + 1;
     ER_CUDA(cudaMalloc(&w->ints, nint * sizeof(int)));
     ER_CUDA(cudaMalloc(&w->counter, (size_t)w->til.n_colblk * sizeof(unsigned)));
@@ -498,7 +498,8 @@ er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er
     if (st != ER_OK) return st;
     bool done = n_active == 0;
     while (!done && !err && it < opt.maxit) {
-        const int todo = std::min(block, opt.maxit - it);
+        int todo = std::min(block, opt.maxit - it);
+        if (fp32 && (todo & 1)) ++todo;  // the FP32 form updates x in iteration pairs
         const bool graphable = use_graph && todo == block;
         if (graphable) {
             if (!w.gexec || w.g_Yt != Yt || w.g_Z != Z || w.g_tol != tol || w.g_iters != block || w.g_parity != cur) {
@@ -516,7 +517,12 @@ er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er
             }
             ER_CUDA(cudaGraphLaunch(w.gexec, w.s));
             pf.launches[ER_PASS_A] += block;
-            pf.launches[ER_PASS_B] += block;
+            if (fp32) {
+                pf.launches[ER_PASS_B] += block / 2;
+                pf.launches[ER_PASS_B0] += block / 2;
+            } else {
+                pf.launches[ER_PASS_B] += block;
+            }
         } else {
             for (int i = 0; i < todo; ++i) cur = iterate(cur, &pf);
         }

@@ -52,7 +52,7 @@ class er_solve_opts(ctypes.Structure):
 class er_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("sweeps", c_int32), ("converged_cols", c_int32),
                 ("k", c_int32), ("max_rel_residual", c_double), ("seconds", c_double),
-                ("launches", c_int32 * 4), ("kernel_ms", c_double * 4)]
+                ("launches", c_int32 * 5), ("kernel_ms", c_double * 5)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -61,7 +61,7 @@ class er_solve_stats(ctypes.Structure):
         return d
 
 
-PASS_A, PASS_B, PASS_R, PASS_OTHER = range(4)
+PASS_A, PASS_B, PASS_R, PASS_OTHER, PASS_B0 = range(5)
 
 
 _S = c_int32  # er_status
