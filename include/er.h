@@ -192,6 +192,30 @@ er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision 
 er_status er_solve_noalloc(er_grid *g, const void *Yt, void *Z, int32_t k, const er_solve_opts *opts,
                            er_solve_stats *stats, void *stream);
 
+typedef struct {
+    int32_t n_grids;
+    int32_t iterations;       /* iterations of the batch (the slowest network) */
+    int32_t replacements;     /* FP64 residual replacements */
+    int32_t converged;        /* networks whose every column met tol */
+    int64_t nodes;            /* non-floating nodes over all networks */
+    double max_rel_residual;  /* final FP64 residual, max over all networks and columns */
+    double seconds;           /* host wall time of the call */
+    int32_t launches;         /* kernels launched */
+    int32_t graph_captures;   /* CUDA graphs captured (one per change of the work list) */
+} er_batch_stats;
+
+/* Batching form: the all-node R maps of n networks (e.g. TSV-placement candidates of
+ * uneven sizes) in shared launches.  Network c is sketched with seed + c, solved in the
+ * FP32 form (the arithmetic of er_solve with ER_FP32_REFINE) and its map written to the
+ * device array R_out[c] [n_c] (FP64).  Every pass of every iteration is ONE launch over a
+ * work list of (network, tile) pairs, captured in a CUDA graph per poll period; networks
+ * leave the work list as they converge.  tile_rows[c] (nullable) overrides the y rows
+ * swept per CTA for network c (the autotuner's choice).  prec must be ER_FP32_REFINE.
+ * Workspace is allocated for the call and freed before it returns.  Synchronises. */
+er_status er_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, er_precision prec,
+                         const int32_t *tile_rows, double *const *R_out, const er_solve_opts *opts,
+                         er_batch_stats *stats, void *stream);
+
 /* R_i = sum_j Z_ij^2 into device array R [n] (FP64); +inf for floating nodes.
  * Z is FP64 or FP32 per `prec`.  Async on `stream`. */
 er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R,

@@ -1,0 +1,81 @@
+"""Autotuner for the stencil passes' tile shape (y rows swept per CTA).
+
+For a network size class (tiers, width, height, k, precision) it times a few PCG
+iterations through the C ABI for each candidate row count, with the library's own
+per-pass CUDA-event timing (er_solve_opts.profile), and keeps the fastest.  Results
+are cached in a JSON file (ER_AUTOTUNE_CACHE, default ~/.cache/er3d_autotune.json),
+keyed by the size class, so each class is measured once per machine.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+CANDIDATE_ROWS = (16, 32, 64, 128)
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("ER_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "er3d_autotune.json"))
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict) -> None:
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def key(inst, k: int, prec: str) -> str:
+    return f"{inst.T}x{inst.W}x{inst.H}_k{k}_{prec}"
+
+
+def measure(inst, k: int, prec: str = "fp32", iters: int = 8, rows_list=CANDIDATE_ROWS) -> dict:
+    """Per-iteration pass time (ms) for each candidate row count on this network."""
+    import torch
+
+    from . import er
+    g = er.grid_create(inst)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    Y = torch.empty((inst.n, k), dtype=dt, device="cuda")
+    Z = torch.empty_like(Y)
+    er.sketch(g, k, 1, prec, Y)
+    out = {}
+    for rows in rows_list:
+        if rows > inst.H and rows != rows_list[0]:
+            continue
+        best = None
+        for _ in range(2):
+            o = er.default_solve_opts(prec, maxit=iters, profile=1, tile_rows=rows, replace_every=10 ** 6)
+            _, st = er.solve(g, Y, Z, k, prec, o, allow_unconverged=True)
+            t = (st["kernel_ms"][er.PASS_A] + st["kernel_ms"][er.PASS_B] + st["kernel_ms"][er.PASS_B0]) / max(
+                st["iterations"], 1)
+            best = t if best is None else min(best, t)
+        out[rows] = best
+    g.destroy()
+    return out
+
+
+def best_rows(inst, k: int, prec: str = "fp32") -> int:
+    """The cached best row count for this size class, measuring it on first use."""
+    kk = key(inst, k, prec)
+    with _lock:
+        d = _load()
+        if kk in d:
+            return int(d[kk]["rows"])
+        times = measure(inst, k, prec)
+        rows = min(times, key=times.get)
+        d[kk] = {"rows": int(rows), "ms_per_iteration": {str(r): t for r, t in times.items()}}
+        _store(d)
+        return int(rows)

@@ -134,9 +134,15 @@ __device__ inline void finalize_column(const KArgs<T, C> &a, int j, double total
         const double rel = a.rho0[j] > 0.0 ? sqrt(total / a.rho0[j]) : 0.0;
         a.resid[j] = rel;
         if (a.rmode == 1 && a.active[j]) {
-            // reliable update: the recursion continues from the recomputed residual
+            // reliable update: the recursion continues from the recomputed residual.  If the
+            // recursion already claims tol while the FP64 residual does not, or it has fallen
+            // more than 100x below the true residual, it ran on past its attainable accuracy
+            // and the search direction is stale: restart it (beta = 0, a refinement sweep on
+            // the correction) instead of rescaling it.
             const double rho = a.rho[j];
-            a.beta[j] = rho > 0.0 ? a.beta[j] * (total / rho) : 0.0;
+            const double rec = a.rho0[j] > 0.0 ? sqrt(rho / a.rho0[j]) : 0.0;
+            const bool stale = !(rho > 0.0) || rho < 1e-4 * total || (!(rec > a.tol) && rel > a.tol);
+            a.beta[j] = stale ? 0.0 : a.beta[j] * (total / rho);
             a.rho[j] = total;
             if (!(rel > a.tol)) {
                 a.active[j] = 0;
@@ -204,8 +210,8 @@ __device__ inline void reduce_and_finalize(const KArgs<T, C> &a, double *sred, i
 // of one spatial tile are adjacent in launch order, so the CTAs that read the same node
 // rows run together and share DRAM pages and the per-node coefficients in L2.
 template <typename T, typename C>
-__device__ inline void decode_block(const KArgs<T, C> &a, int &tx, int &tyi, int &t, int &cb) {
-    int b = blockIdx.x;
+__device__ inline void decode_block(const KArgs<T, C> &a, int block_id, int &tx, int &tyi, int &t, int &cb) {
+    int b = block_id;
     if (a.cb_fast) {
         cb = b % a.n_colblk;
         b /= a.n_colblk;
@@ -272,6 +278,21 @@ struct Prof {
 
 void prof_begin(Workspace &w, Prof *pf, int kind);
 void prof_end(Workspace &w, Prof *pf, int kind);
+
+// One network of a batch: its tensor maps (r0, r1, p0, p1, x, x64, b, coef), its kernel
+// arguments (geometry, coefficients, scalars, partials) and its vectors.
+struct BatchItem {
+    CUtensorMap tm[8];
+    KArgs<float, float> a;
+    float *r[2], *p[2], *c;
+    double *x64;
+    const float *b;
+};
+
+// er_fp32.cu: batched passes (mode = MODE_*) over a work list of (network, block)
+er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, int n_work, int cur, int rmode,
+                          cudaStream_t s);
+er_status fp32_make_map(CUtensorMap *m, bool f64, const void *base, int64_t d0, int box0, const GridDev &g);
 
 // er_pcg.cu: argument checks and the solve loop on a prepared workspace
 er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts &opt);

@@ -118,22 +118,22 @@ __device__ __forceinline__ float f4(const float4 &f, int v) { return v == 0 ? f.
 // centre, south) and the ring (x-neighbours of the centre row); then it publishes v in the
 // ring, synchronises once, and the stage is refilled NS rows ahead.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(const __grid_constant__ TArgs ta) {
+__device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUtensorMap *tm0, const CUtensorMap *tm1,
+                                         const CUtensorMap *tm2, const CUtensorMap *tm3, int block_id,
+                                         unsigned char *smem_raw) {
     using L = Layout<MODE>;
     constexpr int V = 4, KB = kTPN * V;  // 32 columns per CTA
     constexpr bool R64 = MODE == MODE_R;
     using Cv = typename std::conditional<R64, double, float>::type;  // operand type
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     Cv *ring = reinterpret_cast<Cv *>(smem + L::NS * L::BYTES);  // [2][kNX][KB]
     __shared__ __align__(8) uint64_t bars[L::NS];
     __shared__ int s_abort;
     __shared__ __align__(16) float s_beta[KB], s_alpha[KB], s_alpha_prev[KB];  // per-column CG scalars
-    const KArgs<float, float> &a = ta.a;
 
     const int lc = threadIdx.x % kTPN, xl = threadIdx.x / kTPN;
     int tx, tyi, t, cb;
-    decode_block(a, tx, tyi, t, cb);
+    decode_block(a, block_id, tx, tyi, t, cb);
     const int spatial = (t * a.tiles_y + tyi) * a.tiles_x + tx;
     const int c0 = cb * KB;
     const int xb = tx * kTXI - 1;
@@ -164,14 +164,14 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
         const int y = y0 - 1 + ri;
         mbar_arrive_expect_tx(&bars[s], L::BYTES);
         if constexpr (R64) {
-            tma_load4(st + L::OFF_X, &ta.tm[0], &bars[s], c0, xb, y, t);  // x64
-            tma_load4(st + L::OFF_R, &ta.tm[1], &bars[s], c0, xb, y, t);  // b
+            tma_load4(st + L::OFF_X, tm0, &bars[s], c0, xb, y, t);  // x64
+            tma_load4(st + L::OFF_R, tm1, &bars[s], c0, xb, y, t);  // b
         } else {
-            tma_load4(st + L::OFF_R, &ta.tm[0], &bars[s], c0, xb, y, t);
-            tma_load4(st + L::OFF_P, &ta.tm[1], &bars[s], c0, xb, y, t);
-            if constexpr (MODE == MODE_B) tma_load4(st + L::OFF_X, &ta.tm[2], &bars[s], c0, xb, y, t);
+            tma_load4(st + L::OFF_R, tm0, &bars[s], c0, xb, y, t);
+            tma_load4(st + L::OFF_P, tm1, &bars[s], c0, xb, y, t);
+            if constexpr (MODE == MODE_B) tma_load4(st + L::OFF_X, tm2, &bars[s], c0, xb, y, t);
         }
-        tma_load4(st + L::OFF_COEF, &ta.tm[3], &bars[s], 0, xb, y, t);
+        tma_load4(st + L::OFF_COEF, tm3, &bars[s], 0, xb, y, t);
     };
     bool aborted = false;
     auto wait_row = [&](int ri) {
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
 #pragma unroll
     for (int v = 0; v < V; ++v) vn[v] = vc[v] = (Cv)0, rc[v] = 0.f;
 
+#pragma unroll 2
     for (int ri = 0; ri < nrow; ++ri) {
         wait_row(ri);
         const unsigned char *st = smem + (ri % L::NS) * L::BYTES;
@@ -341,13 +342,12 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
                 }
             }
             if constexpr (R64) {
-                const double dinv = fabs((double)cfc.x);
+                const float dinv = fabsf(cfc.x);
                 float ro[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    const double rn = (double)rc[v] - q[v];
-                    ro[v] = (float)rn;
-                    acc[v] = fma(dinv * rn, rn, acc[v]);
+                    ro[v] = (float)((double)rc[v] - q[v]);
+                    run[v] = fmaf(dinv * ro[v], ro[v], run[v]);
                 }
                 stv<float, float, V>(a.r_out + idx, ro);
             } else if constexpr (MODE == MODE_A_DOT) {
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
                 }
                 stv<float, float, V>(a.r_out + idx, rn);
             }
-            if constexpr (!R64) {
+            {
                 if (++nrun == 8) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -416,16 +416,22 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(co
     reduce_and_finalize<float, float, MODE, KB>(a, sred, spatial, cb);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3) k_tma(const __grid_constant__ TArgs ta) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    tma_pass<MODE>(ta.a, &ta.tm[0], &ta.tm[1], &ta.tm[2], &ta.tm[3], (int)blockIdx.x, smem_raw);
+}
+
 // ---------------------------------------------------------------------------------------
 // streaming kernels of the FP32 form (same tiling, no halo)
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_fp32_stream(const KArgs<float, float> a) {
+__device__ __forceinline__ void fp32_stream_pass(const KArgs<float, float> &a, int block_id) {
     constexpr int V = 4, KB = kTPN * V;
     __shared__ double sred[kNX * KB];
     const int lc = threadIdx.x % kTPN, xl = threadIdx.x / kTPN;
     int tx, tyi, t, cb;
-    decode_block(a, tx, tyi, t, cb);
+    decode_block(a, block_id, tx, tyi, t, cb);
     const int spatial = (t * a.tiles_y + tyi) * a.tiles_x + tx;
     const int x = tx * kTXI - 1 + xl;
     const int y0 = tyi * a.rows, y1 = min(y0 + a.rows, a.H);
@@ -475,6 +481,58 @@ __global__ void __launch_bounds__(kThreads) k_fp32_stream(const KArgs<float, flo
     }
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_fp32_stream(const KArgs<float, float> a) {
+    fp32_stream_pass<MODE>(a, (int)blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------------------
+// batching form: one launch per pass covers the tiles of many networks.  The work list
+// holds (network, block-within-network); each CTA copies its network's arguments into
+// shared memory and runs the same pass as the single-network kernels.
+
+template <int MODE>
+__device__ __forceinline__ void batch_args(const BatchItem &it, int cur, int rmode, KArgs<float, float> &a) {
+    a = it.a;
+    a.rmode = rmode;
+    if constexpr (MODE == MODE_R) {
+        a.x64 = it.x64;
+        a.r_out = it.r[cur];
+    } else if constexpr (MODE == MODE_INIT) {
+        a.b_in = it.b; a.r_out = it.r[0]; a.x = it.c; a.p_out = it.p[0]; a.x64 = it.x64;
+    } else if constexpr (MODE == MODE_ACCUM || MODE == MODE_UNSCALE) {
+        a.x = it.c; a.x64 = it.x64;
+    } else {
+        a.r_in = it.r[cur]; a.p_in = it.p[cur]; a.x = it.c;
+        a.r_out = it.r[1 - cur]; a.p_out = it.p[1 - cur];
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3)
+    k_tma_batch(const BatchItem *__restrict__ items, const int2 *__restrict__ work, int cur, int rmode) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ KArgs<float, float> s_a;
+    const int2 wk = work[blockIdx.x];
+    const BatchItem &it = items[wk.x];
+    if (threadIdx.x == 0) batch_args<MODE>(it, cur, rmode, s_a);
+    __syncthreads();
+    if constexpr (MODE == MODE_R)
+        tma_pass<MODE>(s_a, &it.tm[5], &it.tm[6], nullptr, &it.tm[7], wk.y, smem_raw);
+    else
+        tma_pass<MODE>(s_a, &it.tm[cur], &it.tm[2 + cur], &it.tm[4], &it.tm[7], wk.y, smem_raw);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_stream_batch(const BatchItem *__restrict__ items,
+                                                           const int2 *__restrict__ work) {
+    __shared__ KArgs<float, float> s_a;
+    const int2 wk = work[blockIdx.x];
+    if (threadIdx.x == 0) batch_args<MODE>(items[wk.x], 0, 0, s_a);
+    __syncthreads();
+    fp32_stream_pass<MODE>(s_a, wk.y);
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 
@@ -506,7 +564,42 @@ static er_status make_map(CUtensorMap *m, CUtensorMapDataType dt, int esize, con
     return ER_OK;
 }
 
+er_status fp32_make_map(CUtensorMap *m, bool f64, const void *base, int64_t d0, int box0, const GridDev &g) {
+    return f64 ? make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, base, d0, box0, g)
+               : make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, d0, box0, g);
+}
+
 static bool g_attr_done = false;
+static bool g_battr_done = false;
+
+er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, int n_work, int cur, int rmode,
+                          cudaStream_t s) {
+    if (!g_battr_done) {
+        ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_A_DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dyn_smem<MODE_A_DOT>()));
+        ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dyn_smem<MODE_B>()));
+        ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_B0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dyn_smem<MODE_B0>()));
+        ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dyn_smem<MODE_R>()));
+        g_battr_done = true;
+    }
+    if (n_work <= 0) return ER_OK;
+    const unsigned nb = (unsigned)n_work;
+    switch (mode) {
+        case MODE_A_DOT: k_tma_batch<MODE_A_DOT><<<nb, kThreads, dyn_smem<MODE_A_DOT>(), s>>>(items, work, cur, rmode); break;
+        case MODE_B: k_tma_batch<MODE_B><<<nb, kThreads, dyn_smem<MODE_B>(), s>>>(items, work, cur, rmode); break;
+        case MODE_B0: k_tma_batch<MODE_B0><<<nb, kThreads, dyn_smem<MODE_B0>(), s>>>(items, work, cur, rmode); break;
+        case MODE_R: k_tma_batch<MODE_R><<<nb, kThreads, dyn_smem<MODE_R>(), s>>>(items, work, cur, rmode); break;
+        case MODE_INIT: k_stream_batch<MODE_INIT><<<nb, kThreads, 0, s>>>(items, work); break;
+        case MODE_ACCUM: k_stream_batch<MODE_ACCUM><<<nb, kThreads, 0, s>>>(items, work); break;
+        case MODE_UNSCALE: k_stream_batch<MODE_UNSCALE><<<nb, kThreads, 0, s>>>(items, work); break;
+        default: return fail(ER_ERR_INVALID_ARG, "bad batch pass");
+    }
+    ER_CUDA(cudaGetLastError());
+    return ER_OK;
+}
 
 er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z) {
     const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, F64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;

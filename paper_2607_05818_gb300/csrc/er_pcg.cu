@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(const KArgs<T, C> a) {
 
     const int lc = threadIdx.x % kTPN, xl = threadIdx.x / kTPN;
     int tx, tyi, t, cb;
-    decode_block(a, tx, tyi, t, cb);
+    decode_block(a, (int)blockIdx.x, tx, tyi, t, cb);
     const int spatial = (t * a.tiles_y + tyi) * a.tiles_x + tx;
     const int x = tx * kTXI - 1 + xl;
     const int y0 = tyi * a.rows, y1 = min(y0 + a.rows, a.H);
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_stream(const KArgs<T, T> a) {
     __shared__ double sred[SRED];
     const int lc = threadIdx.x % kTPN, xl = threadIdx.x / kTPN;
     int tx, tyi, t, cb;
-    decode_block(a, tx, tyi, t, cb);
+    decode_block(a, (int)blockIdx.x, tx, tyi, t, cb);
     const int spatial = (t * a.tiles_y + tyi) * a.tiles_x + tx;
     const int x = tx * kTXI - 1 + xl;
     const int y0 = tyi * a.rows, y1 = min(y0 + a.rows, a.H);

@@ -64,6 +64,15 @@ class er_solve_stats(ctypes.Structure):
 PASS_A, PASS_B, PASS_R, PASS_OTHER, PASS_B0 = range(5)
 
 
+class er_batch_stats(ctypes.Structure):
+    _fields_ = [("n_grids", c_int32), ("iterations", c_int32), ("replacements", c_int32),
+                ("converged", c_int32), ("nodes", c_int64), ("max_rel_residual", c_double),
+                ("seconds", c_double), ("launches", c_int32), ("graph_captures", c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _S = c_int32  # er_status
 _sig = {
     "er_default_solve_opts": (er_solve_opts, [c_int32]),
@@ -77,6 +86,8 @@ _sig = {
     "er_solve_noalloc": (_S, [c_void_p, c_void_p, c_void_p, c_int32, POINTER(er_solve_opts),
                               POINTER(er_solve_stats), c_void_p]),
     "er_reff_map": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "er_batch_solve": (_S, [POINTER(c_void_p), c_int32, c_int32, c_uint64, c_int32, POINTER(c_int32),
+                            POINTER(c_void_p), POINTER(er_solve_opts), POINTER(er_batch_stats), c_void_p]),
     "er_reff_map_host": (_S, [POINTER(er_tier), c_int32, POINTER(er_tsv), c_int64, POINTER(er_pad), c_int64,
                               c_int32, c_uint64, c_int32, POINTER(er_solve_opts), c_void_p,
                               POINTER(er_solve_stats), c_void_p]),
@@ -230,6 +241,22 @@ def solve_noalloc(grid: Grid, Yt, Z, k: int, opts: er_solve_opts | None = None, 
 def reff_map(grid: Grid, Z, k: int, prec, R, stream=None):
     return _check(_lib.er_reff_map(grid.handle, _ptr(Z), k, PRECISIONS[prec], _ptr(R), _stream(stream)),
                   "er_reff_map")
+
+
+def batch_solve(grids, k: int, seed: int, R_out, prec="fp32", opts: er_solve_opts | None = None,
+                tile_rows=None, stream=None, allow_unconverged=False):
+    """Batching form: R maps of many networks in shared launches; network c uses seed + c.
+    R_out: list of device FP64 tensors (one per grid)."""
+    n = len(grids)
+    hs = (c_void_p * n)(*[g.handle.value if isinstance(g.handle, c_void_p) else g.handle for g in grids])
+    rs = (c_void_p * n)(*[_ptr(r) for r in R_out])
+    tr = (c_int32 * n)(*tile_rows) if tile_rows is not None else None
+    st = er_batch_stats()
+    ok = (ER_OK, ER_ERR_NOT_CONVERGED) if allow_unconverged else (ER_OK,)
+    s = _lib.er_batch_solve(hs, n, k, c_uint64(seed), PRECISIONS[prec], tr, rs,
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(st), _stream(stream))
+    _check(s, "er_batch_solve", ok)
+    return s, st.as_dict()
 
 
 def reff_map_host(inst, k: int, seed: int, prec, opts: er_solve_opts | None = None, R_host=None, stream=None,

@@ -62,6 +62,8 @@ CASES = [
                                                   open_frac=0.35), 20),
     ("single_node", lambda: I.uniform(1, 1, 1, 1.0, 1.0, pads=[(0, 0, 0, 0.5)]), 8),
     ("chain_1x97", lambda: I.random_small(np.random.default_rng(4), T=1, W=97, H=1, n_pads=1), 12),
+    ("small_2x5x3_tsv", lambda: I.random_small(np.random.default_rng(5), T=2, W=5, H=3, n_tsv=4, n_pads=1), 32),
+    ("small_1x5x8", lambda: I.random_small(np.random.default_rng(6), T=1, W=5, H=8, n_pads=1), 8),
 ]
 
 
@@ -98,7 +100,7 @@ def test_fp64_map_matches_oracle(er, name, make, k):
     assert np.all(np.isinf(R[fl])) and np.all(Z[fl] == 0.0)
 
 
-@pytest.mark.parametrize("name,make,k", CASES[:4], ids=[c[0] for c in CASES[:4]])
+@pytest.mark.parametrize("name,make,k", CASES, ids=[c[0] for c in CASES])
 def test_fp32_refine_map_within_1e3(er, name, make, k):
     inst = make()
     seed = 31337
@@ -106,6 +108,7 @@ def test_fp32_refine_map_within_1e3(er, name, make, k):
     _, _, R, st = gpu_map(er, inst, k, seed, "fp32")
     err = rel_err(R, R_ref)
     assert err <= 1e-3, (name, err, st)
+    assert st["max_rel_residual"] <= 1e-7 and st["converged_cols"] == k, (name, st)
 
 
 def test_tiny_plain_exact_and_jl_report(er):
