@@ -216,6 +216,44 @@ er_status er_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
                          const int32_t *tile_rows, double *const *R_out, const er_solve_opts *opts,
                          er_batch_stats *stats, void *stream);
 
+/* ---- learned surrogate: a BF16 U-Net from per-node maps to log R -------------------- */
+
+typedef struct {
+    int32_t in_ch;   /* input channels per node (a multiple of 32; pad with zeros) */
+    int32_t out_ch;  /* outputs per node (log R per tier) */
+    int32_t levels;  /* U-Net levels, 2..8 */
+    int32_t base;    /* channels of level 0 (a multiple of 32); level l has base * 2^l */
+    int32_t H, W;    /* map size, divisible by 2^(levels-1) */
+} er_unet_shape;
+
+typedef struct er_surrogate er_surrogate;  /* opaque; owned by the library */
+
+/* Create a U-Net: encoder levels of two 3x3 conv + ReLU with 2x2 max pooling between
+ * them, decoder levels of nearest 2x upsampling, concatenation with the encoder's
+ * output of the same level and two 3x3 conv + ReLU, and a 1x1 head.  Weights are
+ * He-normal from `seed` (FP32 masters, BF16 copies).  The network is not in the paper:
+ * it is a screening surrogate of the paper's quantity, with er_solve as the judge. */
+er_status er_surrogate_create(const er_unet_shape *shape, uint64_t seed, er_surrogate **out);
+er_status er_surrogate_destroy(er_surrogate *s);
+/* Parameter count, and FP32 parameters in a fixed order (encoder convolutions level by
+ * level, decoder convolutions from the deepest level up, then the head; each layer's
+ * weights [cout][3][3][cin] (head [out_ch][base]) before its biases). */
+er_status er_surrogate_num_params(const er_surrogate *s, int64_t *n);
+er_status er_surrogate_get_params(const er_surrogate *s, float *host, int64_t n);
+er_status er_surrogate_set_params(er_surrogate *s, const float *host, int64_t n);
+/* Forward pass: maps [B][H][W][in_ch] BF16 (device) -> logR [B][H][W][out_ch] FP32
+ * (device).  Asynchronous on `stream`. */
+er_status er_surrogate_infer(er_surrogate *s, const void *maps, int32_t B, float *logR, void *stream);
+/* Forward, masked mean-squared error against target [B][H][W][out_ch] (FP32, device;
+ * mask uint8 of the same shape, nullable: entries with mask 0 are ignored) and
+ * backward; FP32 parameter gradients (same order as the parameters) are copied to
+ * grads_host if it is not NULL, the loss to *loss.  Synchronises. */
+er_status er_surrogate_grad(er_surrogate *s, const void *maps, const float *target, const uint8_t *mask, int32_t B,
+                            float *grads_host, double *loss, void *stream);
+/* er_surrogate_grad followed by one Adam step (beta 0.9/0.999, eps 1e-8) at rate lr. */
+er_status er_surrogate_train_step(er_surrogate *s, const void *maps, const float *target, const uint8_t *mask,
+                                  int32_t B, float lr, double *loss, void *stream);
+
 /* R_i = sum_j Z_ij^2 into device array R [n] (FP64); +inf for floating nodes.
  * Z is FP64 or FP32 per `prec`.  Async on `stream`. */
 er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R,

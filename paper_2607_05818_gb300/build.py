@@ -12,7 +12,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = ["er_grid.cu", "er_pcg.cu", "er_fp32.cu", "er_noalloc.cu", "er_batch.cu"]
+SRC = ["er_grid.cu", "er_pcg.cu", "er_fp32.cu", "er_noalloc.cu", "er_batch.cu", "er_unet_kernels.cu",
+       "er_surrogate.cu"]
 LIB = os.path.join(HERE, "liber.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -36,7 +37,7 @@ def _compile(src: str, obj: str, extra: list[str]) -> str:
 
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     srcs = [os.path.join(HERE, "csrc", s) for s in SRC]
-    hdrs = [os.path.join(HERE, "csrc", h) for h in ("er_internal.h", "er_common.cuh")] + [
+    hdrs = [os.path.join(HERE, "csrc", h) for h in ("er_internal.h", "er_common.cuh", "er_unet.h")] + [
         os.path.join(ROOT, "include", "er.h")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in srcs + hdrs + [__file__])

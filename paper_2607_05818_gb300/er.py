@@ -73,6 +73,11 @@ class er_batch_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class er_unet_shape(ctypes.Structure):
+    _fields_ = [("in_ch", c_int32), ("out_ch", c_int32), ("levels", c_int32), ("base", c_int32), ("H", c_int32),
+                ("W", c_int32)]
+
+
 _S = c_int32  # er_status
 _sig = {
     "er_default_solve_opts": (er_solve_opts, [c_int32]),
@@ -92,6 +97,16 @@ _sig = {
                               c_int32, c_uint64, c_int32, POINTER(er_solve_opts), c_void_p,
                               POINTER(er_solve_stats), c_void_p]),
     "er_release_pool": (_S, []),
+    "er_surrogate_create": (_S, [POINTER(er_unet_shape), c_uint64, POINTER(c_void_p)]),
+    "er_surrogate_destroy": (_S, [c_void_p]),
+    "er_surrogate_num_params": (_S, [c_void_p, POINTER(c_int64)]),
+    "er_surrogate_get_params": (_S, [c_void_p, c_void_p, c_int64]),
+    "er_surrogate_set_params": (_S, [c_void_p, c_void_p, c_int64]),
+    "er_surrogate_infer": (_S, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "er_surrogate_grad": (_S, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, POINTER(c_double),
+                               c_void_p]),
+    "er_surrogate_train_step": (_S, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
+                                     POINTER(c_double), c_void_p]),
     "er_status_str": (ctypes.c_char_p, [c_int32]),
     "er_last_error": (ctypes.c_char_p, []),
 }
@@ -272,6 +287,64 @@ def reff_map_host(inst, k: int, seed: int, prec, opts: er_solve_opts | None = No
                               _stream(stream))
     _check(s, "er_reff_map_host", ok)
     return R, st.as_dict()
+
+
+class Surrogate:
+    """An er_surrogate handle: the BF16 U-Net from per-node maps to log R."""
+
+    def __init__(self, in_ch=32, out_ch=4, levels=6, base=32, H=256, W=256, seed=1):
+        self.shape = er_unet_shape(in_ch, out_ch, levels, base, H, W)
+        h = c_void_p()
+        _check(_lib.er_surrogate_create(ctypes.byref(self.shape), c_uint64(seed), ctypes.byref(h)),
+               "er_surrogate_create")
+        self.handle = h
+        self._steps = 0
+
+    def step_count(self) -> int:
+        """Adam steps taken through this handle."""
+        return self._steps
+
+    def num_params(self) -> int:
+        n = c_int64()
+        _check(_lib.er_surrogate_num_params(self.handle, ctypes.byref(n)), "er_surrogate_num_params")
+        return n.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(_lib.er_surrogate_get_params(self.handle, out.ctypes.data, out.size), "er_surrogate_get_params")
+        return out
+
+    def set_params(self, flat) -> None:
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(_lib.er_surrogate_set_params(self.handle, a.ctypes.data, a.size), "er_surrogate_set_params")
+
+    def infer(self, maps, B, out, stream=None):
+        _check(_lib.er_surrogate_infer(self.handle, _ptr(maps), B, _ptr(out), _stream(stream)), "er_surrogate_infer")
+
+    def grad(self, maps, target, mask, B, stream=None):
+        g = np.empty(self.num_params(), dtype=np.float32)
+        loss = c_double()
+        _check(_lib.er_surrogate_grad(self.handle, _ptr(maps), _ptr(target), _ptr(mask), B, g.ctypes.data,
+                                      ctypes.byref(loss), _stream(stream)), "er_surrogate_grad")
+        return loss.value, g
+
+    def train_step(self, maps, target, mask, B, lr, stream=None) -> float:
+        loss = c_double()
+        _check(_lib.er_surrogate_train_step(self.handle, _ptr(maps), _ptr(target), _ptr(mask), B, ctypes.c_float(lr),
+                                            ctypes.byref(loss), _stream(stream)), "er_surrogate_train_step")
+        self._steps += 1
+        return loss.value
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            _lib.er_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def release_pool():

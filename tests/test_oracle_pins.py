@@ -341,3 +341,47 @@ def test_jl_with_floating_nodes_matches_sampled():
     nodes = np.flatnonzero(~fl)[:6]
     Rs, _ = sketch.reff_jl_sampled(f, Yt, nodes)
     np.testing.assert_allclose(R[nodes], Rs, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ U-Net reference
+
+def test_unet_reference_gradient_matches_finite_differences():
+    """The FP64 U-Net reference's backward pass against central finite differences on a tiny
+    network (2 levels, 2 base channels, 4x4 maps): every parameter."""
+    from oracle.unet_ref import UNetRef
+    net = UNetRef(in_ch=3, out_ch=2, levels=2, base=2)
+    rng = np.random.default_rng(21)
+    flat = rng.normal(0, 0.5, net.num_params())
+    x = rng.normal(0, 1, (2, 4, 4, 3))
+    target = rng.normal(0, 1, (2, 4, 4, 2))
+    mask = rng.random((2, 4, 4, 2)) > 0.2
+    loss, grad, _ = net.loss_and_grad(flat, x, target, mask)
+    h = 1e-6
+    fd = np.zeros_like(flat)
+    for i in range(len(flat)):
+        e = np.zeros_like(flat)
+        e[i] = h
+        fd[i] = (net.loss_and_grad(flat + e, x, target, mask)[0] - net.loss_and_grad(flat - e, x, target, mask)[0]) / (2 * h)
+    np.testing.assert_allclose(grad, fd, rtol=1e-5, atol=1e-8)
+
+
+def test_unet_reference_layers_against_definitions():
+    """conv3x3 against a direct loop; max pooling against a loop; upsampling round trip."""
+    from oracle import unet_ref as U
+    rng = np.random.default_rng(22)
+    x = rng.normal(size=(1, 5, 4, 3))
+    w = rng.normal(size=(2, 3, 3, 3))
+    b = rng.normal(size=2)
+    y = U.conv3x3(x, w, b)
+    for (h, ww, o) in [(0, 0, 0), (4, 3, 1), (2, 1, 0)]:
+        s = b[o]
+        for ky in range(3):
+            for kx in range(3):
+                yy, xx = h + ky - 1, ww + kx - 1
+                if 0 <= yy < 5 and 0 <= xx < 4:
+                    s += x[0, yy, xx, :] @ w[o, ky, kx, :]
+        assert y[0, h, ww, o] == pytest.approx(s, rel=1e-12)
+    z = rng.normal(size=(1, 4, 4, 2))
+    m, _ = U.maxpool(z)
+    assert m[0, 1, 0, 1] == max(z[0, 2, 0, 1], z[0, 2, 1, 1], z[0, 3, 0, 1], z[0, 3, 1, 1])
+    np.testing.assert_allclose(U.upsample_bwd(U.upsample(z)), 4 * z)
