@@ -60,6 +60,43 @@ def candidate(rng, T=4, W=256):
     return I.batch_candidate(rng, T=T, W=W)
 
 
+def bf16_bits(a: np.ndarray) -> np.ndarray:
+    """float32 -> BF16 bit patterns (uint16), round to nearest even (finite inputs)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    return ((u + (0x7FFF + ((u >> 16) & 1))) >> 16).astype(np.uint16)
+
+
+def candidate_at(seed: int, i: int, T: int = 4, W: int = 256):
+    """Candidate i of the seeded set `seed` (its own generator, so any subset can be rebuilt)."""
+    return candidate(np.random.default_rng([seed, i]), T=T, W=W)
+
+
+def _maps_worker(args):
+    seed, lo, hi, T, W, in_ch = args
+    return lo, np.stack([bf16_bits(node_maps(candidate_at(seed, i, T, W), in_ch)) for i in range(lo, hi)])
+
+
+def upload_maps(count: int, seed: int, T: int = 4, W: int = 256, in_ch: int = 32, workers: int = 0, device="cuda"):
+    """Maps of candidates 0..count-1 of the seeded set, encoded by `workers` spawned processes
+    (0: this process) and copied chunk by chunk into one BF16 device tensor [count][W][W][in_ch]."""
+    import torch
+    out = torch.empty((count, W, W, in_ch), dtype=torch.bfloat16, device=device)
+    chunks = [(seed, lo, min(count, lo + 32), T, W, in_ch) for lo in range(0, count, 32)]
+
+    def put(lo, bits):
+        out[lo:lo + bits.shape[0]].view(torch.int16).copy_(torch.from_numpy(bits.view(np.int16)))
+
+    if workers > 0 and len(chunks) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for lo, bits in pool.imap_unordered(_maps_worker, chunks):
+                put(lo, bits)
+    else:
+        for c in chunks:
+            put(*_maps_worker(c))
+    return out
+
+
 def label(nets, k: int, seed: int, chunk: int = 64):
     """Exact-solver labels: R maps of `nets` with the batching form (network c uses seed + c)."""
     import torch
@@ -76,6 +113,35 @@ def label(nets, k: int, seed: int, chunk: int = 64):
         for g in grids:
             g.destroy()
     return out
+
+
+def label_set(count: int, seed: int, k: int, label_seed: int, T: int = 4, W: int = 256, chunk: int = 64,
+              device="cuda"):
+    """Solver labels (log R maps and masks, on the device) of candidates 0..count-1 of the seeded
+    set, rebuilt and solved `chunk` at a time with the batching form.  Returns (tgt, msk,
+    seconds spent in grid creation and solves)."""
+    import torch
+
+    from . import er
+    tgt = torch.empty((count, W, W, T), dtype=torch.float32, device=device)
+    msk = torch.empty((count, W, W, T), dtype=torch.uint8, device=device)
+    solve_s = 0.0
+    for lo in range(0, count, chunk):
+        part = [candidate_at(seed, i, T, W) for i in range(lo, min(count, lo + chunk))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grids = [er.grid_create(n) for n in part]
+        R = [torch.empty(n.n, dtype=torch.float64, device=device) for n in part]
+        er.batch_solve(grids, k, label_seed + lo, R)
+        torch.cuda.synchronize()
+        solve_s += time.perf_counter() - t0
+        for j, (n, r) in enumerate(zip(part, R)):
+            t, m = target_map(r.cpu().numpy(), n)
+            tgt[lo + j].copy_(torch.from_numpy(t))
+            msk[lo + j].copy_(torch.from_numpy(m))
+        for g in grids:
+            g.destroy()
+    return tgt, msk, solve_s
 
 
 def to_device(nets, Rs, in_ch=32):
