@@ -146,6 +146,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
 
 
+def combine_ranks(units, seconds, world, device="cpu"):
+    """Whole-job figures over the ranks: (sum of the units every rank processed, the slowest
+    rank's time).  Each rank works on its own independent problems, so this is the only
+    exchange, and it happens after the timed region."""
+    if world <= 1:
+        return float(units), float(seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n)
+    return float(n.item()), float(t.item())
+
+
 def load_peaks():
     """Measured HBM and BF16 peaks of this GPU model, else the stated fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -226,8 +241,9 @@ def run_batch(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    value = n_ok * args.steps / (ms / 1e3)
+    n_job, s_max = combine_ranks(n_ok, e0.elapsed_time(e1) / 1e3, world, dev)
+    ms = 1e3 * s_max
+    value = n_job * args.steps / s_max
     # sequential: each candidate's sketch + solve + map on its own (second call, warm workspace)
     nmax = max(c.n for c in cands)
     Y = torch.empty(nmax * k, dtype=torch.float32, device=dev)
@@ -364,7 +380,8 @@ def run_surrogate(args, rank, world, local_rank):
     ver_s = statistics.median(r[2] for r in recs)
     flagged, (insts, Rv), stats = recs[-1][3], recs[-1][4], recs[-1][5]
     step_s = fwd_s + ver_s
-    value = args.sur_screen * n_nodes / step_s
+    n_job, s_max = combine_ranks(args.sur_screen * n_nodes, step_s, world, dev)
+    value = n_job / s_max
     exact = len(insts) * n_nodes / ver_s
     nv = len(flagged) // 2
     pn = pred.index_select(0, torch.as_tensor(flagged, device=dev)).cpu().numpy()
@@ -452,17 +469,9 @@ def run_ours(args, rank, world, local_rank):
             stats.append(step())
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        nt = torch.tensor([float(n_ok)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(nt)
-        n_total = float(nt.item())
-    else:
-        n_total = float(n_ok)
-    value = n_total * args.steps / (ms / 1e3)
+    n_total, s_max = combine_ranks(n_ok, e0.elapsed_time(e1) / 1e3, world, dev)
+    ms = 1e3 * s_max
+    value = n_total * args.steps / s_max
 
     # per-pass durations measured live (CUDA events on the solver stream) in the timed region
     launches = np.sum([s["launches"] for s in stats], axis=0)
