@@ -65,6 +65,29 @@ def sketch_numpy(inst, k, seed):
     return Yt
 
 
+def sketch_rows(inst, nodes, k, seed):
+    """Rows `nodes` (distinct) of Y^T, (len(nodes), k) FP64: each row is the sum over its
+    node's conducting edges of +-sqrt(w_e) Q[:, e] (pad edges +), so a few rows of a
+    network too large for sketch_numpy cost one pass over the edge list."""
+    nodes = np.asarray(nodes, dtype=np.int64)
+    if len(np.unique(nodes)) != len(nodes):
+        raise ValueError("nodes must be distinct")
+    order = np.argsort(nodes)
+    srt = nodes[order]
+    u, v, w, eid, pu, pw, peid = network.edge_list(inst)
+    out = np.zeros((len(nodes), k))
+    rk = 1.0 / np.sqrt(k)
+    for ends, sign in ((u, 1.0), (v, -1.0)):
+        sel = np.flatnonzero(np.isin(ends, srt) & (w > 0))
+        q = rademacher(seed, eid[sel], k) * (sign * np.sqrt(w[sel]) * rk)[:, None]
+        np.add.at(out, order[np.searchsorted(srt, ends[sel])], q)
+    sel = np.flatnonzero(np.isin(pu, srt) & (pw > 0))
+    q = rademacher(seed, peid[sel], k) * (np.sqrt(pw[sel]) * rk)[:, None]
+    np.add.at(out, order[np.searchsorted(srt, pu[sel])], q)
+    out[network.floating_mask(inst)[nodes]] = 0.0
+    return out
+
+
 _LIB = None
 
 

@@ -248,6 +248,19 @@ def test_sketch_c_matches_numpy(oracle_c_built):
                                        rtol=0, atol=1e-14)
 
 
+def test_sketch_rows_match_full_sketch():
+    """Sampled rows (a per-node gather over incident edges) equal the full sketch's rows (an
+    edge-major scatter), floating nodes and nodes with pads and TSVs included."""
+    rng = np.random.default_rng(31)
+    for _ in range(4):
+        inst = I.random_small(rng, open_frac=0.25)
+        Y = sketch.sketch_numpy(inst, 8, 17)
+        nodes = rng.permutation(inst.n)[: max(1, inst.n // 2)]
+        np.testing.assert_allclose(sketch.sketch_rows(inst, nodes, 8, 17), Y[nodes], rtol=0, atol=1e-14)
+    with pytest.raises(ValueError):
+        sketch.sketch_rows(inst, [0, 0], 8, 17)
+
+
 def test_sketch_structure():
     """Mesh rows of M sum to zero over nodes, so the column sums of Y^T are the pad terms alone;
     entries are sums of +-sqrt(w/k) with the canonical sign convention."""
