@@ -242,12 +242,15 @@ er_status er_surrogate_num_params(const er_surrogate *s, int64_t *n);
 er_status er_surrogate_get_params(const er_surrogate *s, float *host, int64_t n);
 er_status er_surrogate_set_params(er_surrogate *s, const float *host, int64_t n);
 /* Forward pass: maps [B][H][W][in_ch] BF16 (device) -> logR [B][H][W][out_ch] FP32
- * (device).  Asynchronous on `stream`. */
+ * (device).  The 3x3 convolutions run on the tcgen05 tensor cores with the accumulator
+ * in tensor memory; their waits are bounded.  Synchronises `stream` at the end and returns
+ * ER_ERR_TIMEOUT if a bounded wait expired. */
 er_status er_surrogate_infer(er_surrogate *s, const void *maps, int32_t B, float *logR, void *stream);
 /* Forward, masked mean-squared error against target [B][H][W][out_ch] (FP32, device;
  * mask uint8 of the same shape, nullable: entries with mask 0 are ignored) and
  * backward; FP32 parameter gradients (same order as the parameters) are copied to
- * grads_host if it is not NULL, the loss to *loss.  Synchronises. */
+ * grads_host if it is not NULL, the loss to *loss.  Synchronises; ER_ERR_TIMEOUT as for
+ * er_surrogate_infer. */
 er_status er_surrogate_grad(er_surrogate *s, const void *maps, const float *target, const uint8_t *mask, int32_t B,
                             float *grads_host, double *loss, void *stream);
 /* er_surrogate_grad followed by one Adam step (beta 0.9/0.999, eps 1e-8) at rate lr. */

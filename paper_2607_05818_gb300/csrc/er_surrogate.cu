@@ -72,6 +72,15 @@ namespace er {
 
 static er_status sur_fail_cuda(cudaError_t e, const char *what) { return cuda_fail(e, what); }
 
+// synchronises `cs` and reports a kernel whose bounded wait expired
+static er_status check_kernels(cudaStream_t cs) {
+    int word = 0;
+    cudaError_t e = unet_take_error(&word, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "unet_take_error");
+    if (word) return fail(ER_ERR_TIMEOUT, "a U-Net kernel's bounded wait expired");
+    return ER_OK;
+}
+
 #define SUR_CUDA(call)                                                  \
     do {                                                                \
         cudaError_t _e = (call);                                        \
@@ -165,7 +174,10 @@ static er_status forward(er_surrogate *s, const __nv_bfloat16 *maps, int B, cuda
     for (int l = L - 2; l >= 0; --l) {
         const int h = s->da[l].h, w = s->da[l].w, c = s->da[l].c;
         const __nv_bfloat16 *below = l == L - 2 ? s->eb[L - 1].a : s->db[l + 1].a;
-        SUR_CUDA(unet_conv3x3(fwd_conv(s->dec[2 * l], below, lvl_ch(s, l + 1), 1, s->eb[l].a, c, B, h, w, s->da[l].a), st));
+        // the upsampled path is written once at full resolution so that the convolution's
+        // operand boxes can be fetched by the TMA
+        SUR_CUDA(unet_upsample2x(below, s->scratch, B, h, w, lvl_ch(s, l + 1), st));
+        SUR_CUDA(unet_conv3x3(fwd_conv(s->dec[2 * l], s->scratch, lvl_ch(s, l + 1), 0, s->eb[l].a, c, B, h, w, s->da[l].a), st));
         SUR_CUDA(unet_conv3x3(fwd_conv(s->dec[2 * l + 1], s->da[l].a, c, 0, nullptr, 0, B, h, w, s->db[l].a), st));
     }
     const int64_t M = (int64_t)B * s->shape.H * s->shape.W;
@@ -425,7 +437,7 @@ er_status er_surrogate_infer(er_surrogate *s, const void *maps, int32_t B, float
     if (st != ER_OK) return st;
     ER_CUDA(cudaMemcpyAsync(logR, s->out, (size_t)B * s->shape.H * s->shape.W * s->shape.out_ch * 4,
                             cudaMemcpyDeviceToDevice, cs));
-    return ER_OK;
+    return er::check_kernels(cs);
 }
 
 er_status er_surrogate_grad(er_surrogate *s, const void *maps, const float *target, const uint8_t *mask, int32_t B,
@@ -448,8 +460,7 @@ er_status er_surrogate_grad(er_surrogate *s, const void *maps, const float *targ
             off += p.second;
         }
     }
-    ER_CUDA(cudaStreamSynchronize(cs));
-    return ER_OK;
+    return er::check_kernels(cs);
 }
 
 er_status er_surrogate_train_step(er_surrogate *s, const void *maps, const float *target, const uint8_t *mask,

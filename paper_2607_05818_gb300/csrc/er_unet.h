@@ -22,7 +22,18 @@ struct UConv {
     int c1o = 0, m1_half = 0;
 };
 
+// 3x3 convolution (forward, or dgrad when y is null) on tcgen05 with the accumulator in
+// tensor memory; needs c1 and c1 + c2 multiples of 32 and cout a multiple of 32.  Inputs
+// stored at full resolution and image sizes that tile into 128-pixel boxes take the
+// persistent TMA kernel, the rest the cp.async-staged one.
 cudaError_t unet_conv3x3(const UConv &c, cudaStream_t s);
+cudaError_t unet_conv3x3_stage(const UConv &c, cudaStream_t s);
+// nearest 2x upsampling [n][h/2][w/2][c] -> [n][h][w][c] (c a multiple of 8)
+cudaError_t unet_upsample2x(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s);
+// the same on warp-level mma.sync
+cudaError_t unet_conv3x3_mma(const UConv &c, cudaStream_t s);
+// copy the kernels' error word (non-zero: a bounded wait expired) to *host, clear it, sync
+cudaError_t unet_take_error(int *host, cudaStream_t s);
 cudaError_t unet_wgrad3x3(const UConv &c, const __nv_bfloat16 *dy, float *dw, cudaStream_t s);
 cudaError_t unet_maxpool(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s);
 cudaError_t unet_maxpool_bwd(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int nb, int h, int w,

@@ -10,8 +10,11 @@
 // nearest-neighbour upsampling on the fly, so neither the concatenation nor the upsampled
 // tensor is ever written.  Operand tiles are staged with cp.async (zero fill outside the
 // image) and fed to the tensor cores with ldmatrix from XOR-swizzled shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "er_internal.h"
@@ -218,6 +221,519 @@ __global__ void __launch_bounds__(256) k_conv3x3(const ConvArgs a) {
                 }
             }
         }
+}
+
+// ---------------------------------------------------------------------------------------
+// 3x3 convolution on the 5th-generation tensor cores (tcgen05): the same implicit GEMM and
+// epilogue as k_conv3x3, with the FP32 accumulator in tensor memory.
+//
+// CTA: 128 pixels (UMMA M = 128) x bn output channels (bn <= 256, a multiple of 16), 4 warps.
+// K advances 32 input channels of one (ky, kx) per stage.  All threads stage A (im2col rows)
+// and B (weight rows) with cp.async into 64-byte rows in the hardware's 64-byte swizzle
+// (16-byte chunk c of row r at c ^ ((r >> 1) & 3), 1024-byte aligned tiles); thread 0
+// issues two kind::f16 MMAs (K = 16 each) per stage and commits them to the stage's
+// mbarrier, which the loaders wait on before refilling that stage.  The epilogue reads the
+// accumulator rows with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = pixels).
+// Every wait is bounded in time; on expiry the kernel sets *err and exits cleanly.
+
+constexpr int TBM = 128, TBK = 32, TSTAGES = 6;
+__device__ int g_err;  // set by a bounded wait that expired; read and cleared by unet_take_error
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase of parity `parity` to complete; false after kWaitNs
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_test(b, parity))
+        if (gtimer() - t0 > kWaitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 64-byte rows, 8-row groups
+// 512 bytes apart (stride byte offset), descriptor version 1, swizzle mode 4 (64B)
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N >> 3, M >> 4
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int bn, int tcols, int *err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t bars[TSTAGES + 1];  // per stage: its MMAs done; [TSTAGES]: all MMAs done
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_s;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    constexpr int ASZ = TBM * TBK * 2;  // 8 KiB
+    const int bsz = bn * TBK * 2;
+    unsigned char *As = smem;
+    unsigned char *Bs = smem + TSTAGES * ASZ;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t M = (int64_t)a.nb * a.h * a.wd;
+    const int64_t m0 = (int64_t)blockIdx.x * TBM;
+    const int n0 = blockIdx.y * bn;
+    const int cin = a.c1 + a.c2;
+    const int cblk = cin / TBK;
+    const int kblocks = 9 * cblk;
+
+    if (tid == 0) {
+        for (int s = 0; s <= TSTAGES; ++s) mbar_init(&bars[s], 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // this thread's four A rows (pixels r = tid/4 + 32 i) and its 16-byte chunk (tid % 4)
+    const int ch = tid & 3;
+    int py[4], px[4], pn[4];
+    bool pv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t m = m0 + (tid >> 2) + 32 * i;
+        pv[i] = m < M;
+        const int64_t mm = pv[i] ? m : 0;
+        px[i] = (int)(mm % a.wd);
+        py[i] = (int)((mm / a.wd) % a.h);
+        pn[i] = (int)(mm / ((int64_t)a.wd * a.h));
+    }
+
+    auto load_stage = [&](int kb, int s) {
+        const int kk = kb / cblk, ci0 = (kb % cblk) * TBK;
+        const int ky = kk / 3 - 1, kx = kk % 3 - 1;
+        unsigned char *at = As + s * ASZ;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = (tid >> 2) + 32 * i;
+            const int ys = py[i] + ky, xs = px[i] + kx;
+            const bool in = pv[i] && ys >= 0 && ys < a.h && xs >= 0 && xs < a.wd;
+            const __nv_bfloat16 *src = a.x1;
+            if (in) {
+                if (ci0 < a.c1) {
+                    src = a.x1_half
+                              ? a.x1 + (((int64_t)pn[i] * (a.h >> 1) + (ys >> 1)) * (a.wd >> 1) + (xs >> 1)) * a.c1 + ci0 + ch * 8
+                              : a.x1 + (((int64_t)pn[i] * a.h + ys) * a.wd + xs) * a.c1 + ci0 + ch * 8;
+                } else {
+                    src = a.x2 + (((int64_t)pn[i] * a.h + ys) * a.wd + xs) * a.c2 + (ci0 - a.c1) + ch * 8;
+                }
+            }
+            cp_async16(at + r * 64 + ((ch ^ ((r >> 1) & 3)) << 4), src, in);
+        }
+        unsigned char *bt = Bs + s * bsz;
+        for (int r = tid >> 2; r < bn; r += 32) {
+            const int co = n0 + r;
+            const bool in = co < a.cout;
+            const __nv_bfloat16 *src = in ? a.w + ((int64_t)co * 9 + kk) * cin + ci0 + ch * 8 : a.w;
+            cp_async16(bt + r * 64 + ((ch ^ ((r >> 1) & 3)) << 4), src, in);
+        }
+    };
+
+    constexpr int PF = TSTAGES - 2;  // stages loaded ahead
+    for (int s = 0; s < PF; ++s) {
+        if (s < kblocks) load_stage(s, s);
+        cp_async_commit();
+    }
+    const uint32_t idesc = idesc_bf16_f32(TBM, bn);
+    bool ok = true;
+    for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % TSTAGES;
+        cp_async_wait<PF - 1>();  // this thread's copies of stage kb have landed
+        fence_proxy_async();      // make them visible to the tensor core's (async proxy) reads
+        __syncthreads();
+        if (abort_s) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ab = saddr(As + s * ASZ), bb = saddr(Bs + s * bsz);
+#pragma unroll
+            for (int k16 = 0; k16 < TBK / 16; ++k16)
+                tc_mma(tmem, sdesc_k_sw64(ab + k16 * 32), sdesc_k_sw64(bb + k16 * 32), idesc, (kb | k16) != 0);
+            tc_commit(&bars[s]);
+        }
+        // refill the stage read by the MMAs of kb - 2 with stage kb + PF
+        const int nk = kb + PF;
+        if (nk < kblocks) {
+            if (kb >= 2) {
+                const int pk = kb - 2;
+                if (!mbar_wait_bounded(&bars[pk % TSTAGES], (uint32_t)((pk / TSTAGES) & 1))) {
+                    atomicExch(err, 1);
+                    abort_s = 1;
+                }
+            }
+            if (!abort_s) load_stage(nk, nk % TSTAGES);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (tid == 0) tc_commit(&bars[TSTAGES]);  // arrives when every MMA issued above is done
+    const bool done = mbar_wait_bounded(&bars[TSTAGES], 0);
+    if (!done) atomicExch(err, 2);
+    tc_fence_after();
+    __syncthreads();
+    ok = ok && done && !abort_s;
+
+    if (ok) {
+        const int row = warp * 32 + lane;
+        const int64_t m = m0 + row;
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            const int co = n0 + c0;
+            if (m >= M || co >= a.cout) continue;
+            __align__(16) __nv_bfloat16 o[16];
+            if (a.y) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float x = v[j] + (a.bias ? a.bias[co + j] : 0.f);
+                    if (a.relu) x = fmaxf(x, 0.f);
+                    o[j] = __float2bfloat16(x);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(a.y + m * a.cout + co);
+                dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+                dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+            } else {
+                const int x = (int)(m % a.wd), y = (int)((m / a.wd) % a.h), nn = (int)(m / ((int64_t)a.wd * a.h));
+                const __nv_bfloat16 *mk;
+                __nv_bfloat16 *dst;
+                if (co < a.c1o) {
+                    mk = a.m1_half ? a.m1 + (((int64_t)nn * (a.h >> 1) + (y >> 1)) * (a.wd >> 1) + (x >> 1)) * a.c1o + co
+                                   : a.m1 + m * a.c1o + co;
+                    dst = a.g1 + m * a.c1o + co;
+                } else {
+                    const int c2o = a.cout - a.c1o;
+                    mk = a.m2 + m * c2o + (co - a.c1o);
+                    dst = a.g2 + m * c2o + (co - a.c1o);
+                }
+                __align__(16) __nv_bfloat16 mv[16];
+                reinterpret_cast<uint4 *>(mv)[0] = reinterpret_cast<const uint4 *>(mk)[0];
+                reinterpret_cast<uint4 *>(mv)[1] = reinterpret_cast<const uint4 *>(mk)[1];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(__bfloat162float(mv[j]) > 0.f ? v[j] : 0.f);
+                reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// 3x3 convolution, persistent and warp-specialised: TMA -> shared memory -> tcgen05.mma ->
+// tensor memory -> epilogue.  One CTA per SM walks output tiles of 128 pixels x bn
+// channels (tile t: pixel block t / tiles_n, channel block t % tiles_n).
+//   warp 0 (one thread)  producer: per K step (BK channels of one tap (ky, kx)) one 4-D TMA
+//                        box of the input [n][y][x][c] at (ci, x0+kx-1, y0+ky-1, n0) -- the
+//                        tap's shifted pixel window, zero-filled outside the image -- and
+//                        one 2-D box of the weights [cout][9 cin], into stage s of a ring
+//   warp 1               allocates 2 x bnp TMEM columns; one thread issues BK/16 MMAs per
+//                        stage (M = 128, N = bn, K = 16) into accumulator tile % 2 and
+//                        commits them to the stage's "empty" barrier, and each finished
+//                        tile to its accumulator's "full" barrier
+//   warps 2-5            epilogue: tcgen05.ld of their TMEM lane quarter, bias + ReLU (or
+//                        the dgrad masks), BF16 stores; then release the accumulator
+// The pixel block (bimg images x by rows x bx columns = 128) is a box of the tensor, so the
+// 128 accumulator rows are the consecutive pixels m0 .. m0+127.  Operands are K-major with
+// the 64-byte (BK = 32) or 128-byte (BK = 64) swizzle, written so by the TMA.  Every wait
+// is bounded in time; on expiry the kernel records *err, stops all roles and frees TMEM.
+
+struct TcArgs {
+    const float *bias;
+    int relu;
+    __nv_bfloat16 *y;
+    __nv_bfloat16 *g1, *g2;
+    const __nv_bfloat16 *m1, *m2;
+    int c1o, m1_half;
+    int nb, h, wd, cout;
+    int c1, c2;                  // channels read through map 0 and map 1
+    int bn, bnp;                 // output channels per tile; TMEM columns per accumulator
+    int tiles_n, tiles;
+    int stages;
+    int *err;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void tma_box4(void *dst, const CUtensorMap *m, uint64_t *bar, int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_box2(void *dst, const CUtensorMap *m, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(saddr(bar))
+        : "memory");
+}
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t *b, uint32_t parity, volatile int *abort_flag, int *err) {
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_test(b, parity)) {
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            atomicExch(err, 1);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// K-major operand descriptors: 64-byte swizzle (8-row groups 512 B apart, mode 4) or
+// 128-byte swizzle (1024 B apart, mode 2)
+template <int BK>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t addr) {
+    constexpr uint64_t sbo = BK == 64 ? 1024 : 512, mode = BK == 64 ? 2 : 4;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46) |
+           (mode << 61);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(192, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtensorMap mx2,
+              const __grid_constant__ CUtensorMap mw, const TcArgs a) {
+    extern __shared__ unsigned char tcv_smem_raw[];
+    constexpr int kMaxStages = 8;
+    __shared__ uint64_t full[kMaxStages], empty[kMaxStages], tfull[2], tempty[2], mdone;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_s;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(tcv_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    constexpr int ABYTES = TBM * BK * 2;
+    const int bbytes = a.bn * BK * 2;
+    const int stg = ABYTES + bbytes;
+    const int S = a.stages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cin = a.c1 + a.c2;
+    const int cblk = cin / BK;
+    const int kblocks = 9 * cblk;
+    const int64_t HW = (int64_t)a.h * a.wd, M = (int64_t)a.nb * HW;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(&mdone, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(2 * a.bnp)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            int last[kMaxStages];
+            for (int s = 0; s < kMaxStages; ++s) last[s] = -1;
+            for (int tile = blockIdx.x; tile < a.tiles && !abort_s; tile += gridDim.x) {
+                const int64_t m0 = (int64_t)(tile / a.tiles_n) * TBM;
+                const int n0 = (tile % a.tiles_n) * a.bn;
+                const int img = (int)(m0 / HW);
+                const int y0 = (int)((m0 % HW) / a.wd), x0 = (int)(m0 % a.wd);
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % S;
+                    if (!wait_or_abort(&empty[s], (uint32_t)(((it / S) & 1) ^ 1), &abort_s, a.err)) break;
+                    unsigned char *st = smem + s * stg;
+                    mbar_expect_tx(&full[s], (uint32_t)stg);
+                    const int kk = kb / cblk, ci0 = (kb % cblk) * BK;
+                    const int xs = x0 + kk % 3 - 1, ys = y0 + kk / 3 - 1;
+                    if (ci0 < a.c1) tma_box4(st, &mx1, &full[s], ci0, xs, ys, img);
+                    else tma_box4(st, &mx2, &full[s], ci0 - a.c1, xs, ys, img);
+                    tma_box2(st + ABYTES, &mw, &full[s], kk * cin + ci0, n0);
+                    last[s] = it;
+                }
+            }
+            // every load issued must land before the CTA exits
+            for (int s = 0; s < S; ++s)
+                if (last[s] >= 0) {
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_test(&full[s], (uint32_t)((last[s] / S) & 1)) && gtimer() - t0 < kWaitNs) {
+                    }
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(TBM, a.bn);
+            int it = 0, tc = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < a.tiles && ok; tile += gridDim.x, ++tc) {
+                const int buf = tc & 1;
+                if (!wait_or_abort(&tempty[buf], (uint32_t)(((tc >> 1) & 1) ^ 1), &abort_s, a.err)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * a.bnp);
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % S;
+                    if (!wait_or_abort(&full[s], (uint32_t)((it / S) & 1), &abort_s, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ab = saddr(smem + s * stg), bb = ab + ABYTES;
+#pragma unroll
+                    for (int k16 = 0; k16 < BK / 16; ++k16)
+                        tc_mma(d, sdesc_k<BK>(ab + k16 * 32), sdesc_k<BK>(bb + k16 * 32), idesc, (kb | k16) != 0);
+                    tc_commit(&empty[s]);
+                }
+                if (ok) tc_commit(&tfull[buf]);
+            }
+            // all MMAs issued above complete before TMEM is released
+            tc_commit(&mdone);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_test(&mdone, 0) && gtimer() - t0 < kWaitNs) {
+            }
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lane quarter this warp may read
+        int tc = 0;
+        for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++tc) {
+            const int buf = tc & 1;
+            if (!wait_or_abort(&tfull[buf], (uint32_t)((tc >> 1) & 1), &abort_s, a.err)) break;
+            tc_fence_after();
+            const int64_t m = (int64_t)(tile / a.tiles_n) * TBM + q * 32 + lane;
+            const int n0 = (tile % a.tiles_n) * a.bn;
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.bnp);
+            for (int c0 = 0; c0 < a.bn; c0 += 16) {
+                float v[16];
+                tc_ld16(tbase + (uint32_t)c0, v);
+                const int co = n0 + c0;
+                if (m >= M) continue;
+                __align__(16) __nv_bfloat16 o[16];
+                if (a.y) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float x = v[j] + (a.bias ? a.bias[co + j] : 0.f);
+                        if (a.relu) x = fmaxf(x, 0.f);
+                        o[j] = __float2bfloat16(x);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + m * a.cout + co);
+                    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+                    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+                } else {
+                    const int x = (int)(m % a.wd), y = (int)((m / a.wd) % a.h), nn = (int)(m / HW);
+                    const __nv_bfloat16 *mk;
+                    __nv_bfloat16 *dst;
+                    if (co < a.c1o) {
+                        mk = a.m1_half ? a.m1 + (((int64_t)nn * (a.h >> 1) + (y >> 1)) * (a.wd >> 1) + (x >> 1)) * a.c1o + co
+                                       : a.m1 + m * a.c1o + co;
+                        dst = a.g1 + m * a.c1o + co;
+                    } else {
+                        const int c2o = a.cout - a.c1o;
+                        mk = a.m2 + m * c2o + (co - a.c1o);
+                        dst = a.g2 + m * c2o + (co - a.c1o);
+                    }
+                    __align__(16) __nv_bfloat16 mv[16];
+                    reinterpret_cast<uint4 *>(mv)[0] = reinterpret_cast<const uint4 *>(mk)[0];
+                    reinterpret_cast<uint4 *>(mv)[1] = reinterpret_cast<const uint4 *>(mk)[1];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(__bfloat162float(mv[j]) > 0.f ? v[j] : 0.f);
+                    reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                    reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.bnp) : "memory");
+    }
+}
+
+// nearest 2x upsampling [n][h/2][w/2][c] -> [n][h][w][c], 16 bytes per thread
+__global__ void k_upsample2x(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // 8-channel chunk of y
+    const int cc = c / 8;
+    const int64_t total = (int64_t)nb * h * w * cc;
+    if (i >= total) return;
+    const int ch = (int)(i % cc);
+    const int64_t p = i / cc;
+    const int xx = (int)(p % w), yy = (int)((p / w) % h), n = (int)(p / ((int64_t)w * h));
+    reinterpret_cast<uint4 *>(y)[i] =
+        reinterpret_cast<const uint4 *>(x)[(((int64_t)n * (h >> 1) + (yy >> 1)) * (w >> 1) + (xx >> 1)) * cc + ch];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -524,7 +1040,208 @@ __global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, __nv_bfloat16 *d
 
 static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+static int *err_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    static int *addr[64] = {};
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, unet::g_err) == cudaSuccess) addr[dev] = static_cast<int *>(p);
+    }
+    return addr[dev];
+}
+
+cudaError_t unet_take_error(int *host, cudaStream_t s) {
+    int *w = err_word();
+    if (!w) return cudaErrorInvalidSymbol;
+    cudaError_t e = cudaMemcpyAsync(host, w, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+// output-channel tile of the tensor-memory kernel: the widest of 256, 192, 128, 96, 64, 32
+// that divides cout and still gives two CTAs per SM; else the narrowest that divides
+static int tc_tile_n(int64_t mtiles, int cout) {
+    const int cands[] = {256, 192, 128, 96, 64, 32};
+    int pick = 0;
+    for (int bn : cands) {
+        if (bn > cout || cout % bn) continue;
+        pick = bn;
+        if (mtiles * (cout / bn) >= 2 * 152) break;
+    }
+    return pick;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// BF16 tensor map, dims innermost first, byte strides of dims 1.., zero fill outside
+static cudaError_t bf16_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims,
+                            const cuuint64_t *strides, const cuuint32_t *box, CUtensorMapSwizzle swz) {
+    auto fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidResourceHandle;  // distinct from launch errors
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        return 0;
+    return n;
+}
+
+// pixel box of 128 consecutive pixels: bimg images x by rows x bx columns
+static bool tc_pixel_box(int h, int w, int &bx, int &by, int &bimg) {
+    if (w >= 128) {
+        if (w % 128) return false;
+        bx = 128, by = 1, bimg = 1;
+        return true;
+    }
+    if (128 % w) return false;
+    bx = w;
+    const int rows = 128 / w;
+    if (h >= rows) {
+        if (h % rows) return false;
+        by = rows, bimg = 1;
+        return true;
+    }
+    if (rows % h) return false;
+    by = h, bimg = rows / h;
+    return true;
+}
+
+template <int BK>
+static cudaError_t launch_conv_tc(const UConv &c, int bx, int by, int bimg, cudaStream_t s) {
+    using namespace unet;
+    const int cin = c.c1 + c.c2;
+    const int64_t M = (int64_t)c.nb * c.h * c.w_;
+    const int64_t tiles_m = (M + TBM - 1) / TBM;
+    const int nsm = sm_count();
+    if (nsm <= 0) return cudaErrorUnknown;
+    int bn = 0;
+    for (int cand : {256, 192, 128, 96, 64, 32}) {
+        if (cand > c.cout || c.cout % cand) continue;
+        bn = cand;
+        if (tiles_m * (c.cout / cand) >= nsm) break;
+    }
+    if (bn == 0) return cudaErrorInvalidValue;
+    const int bnp = bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
+    const int stg = TBM * BK * 2 + bn * BK * 2;
+    const int stages = std::min(8, (200 * 1024) / stg);
+    if (stages < 2) return cudaErrorInvalidValue;
+    const int smem = stages * stg + 1024;
+    // dynamic plus static shared memory must fit the opt-in limit; stages * stg <= 200 KiB
+    constexpr int kMaxDyn = 200 * 1024 + 1024;
+    static bool attr[2] = {false, false};
+    if (!attr[BK == 64]) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+        if (e != cudaSuccess) return e;
+        attr[BK == 64] = true;
+    }
+    const CUtensorMapSwizzle swz = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUtensorMap mx1, mx2, mw;
+    const cuuint32_t xbox[4] = {(cuuint32_t)BK, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bimg};
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)c.c1, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
+        const cuuint64_t str[3] = {(cuuint64_t)c.c1 * 2, (cuuint64_t)c.c1 * 2 * c.w_, (cuuint64_t)c.c1 * 2 * c.w_ * c.h};
+        cudaError_t e = bf16_map(&mx1, c.x1, 4, dims, str, xbox, swz);
+        if (e != cudaSuccess) return e;
+    }
+    if (c.c2 > 0) {
+        const cuuint64_t dims[4] = {(cuuint64_t)c.c2, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
+        const cuuint64_t str[3] = {(cuuint64_t)c.c2 * 2, (cuuint64_t)c.c2 * 2 * c.w_, (cuuint64_t)c.c2 * 2 * c.w_ * c.h};
+        cudaError_t e = bf16_map(&mx2, c.x2, 4, dims, str, xbox, swz);
+        if (e != cudaSuccess) return e;
+    } else {
+        mx2 = mx1;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)9 * cin, (cuuint64_t)c.cout};
+        const cuuint64_t str[1] = {(cuuint64_t)9 * cin * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)bn};
+        cudaError_t e = bf16_map(&mw, c.w, 2, dims, str, box, swz);
+        if (e != cudaSuccess) return e;
+    }
+    TcArgs a{};
+    a.bias = c.bias; a.relu = c.relu; a.y = c.y;
+    a.g1 = c.g1; a.g2 = c.g2; a.m1 = c.m1; a.m2 = c.m2; a.c1o = c.c1o; a.m1_half = c.m1_half;
+    a.nb = c.nb; a.h = c.h; a.wd = c.w_; a.cout = c.cout;
+    a.c1 = c.c1; a.c2 = c.c2; a.bn = bn; a.bnp = bnp;
+    a.tiles_n = c.cout / bn;
+    const int64_t tiles = tiles_m * a.tiles_n;
+    if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
+    a.tiles = (int)tiles;
+    a.stages = stages;
+    a.err = err_word();
+    if (!a.err) return cudaErrorInvalidSymbol;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
+    k_conv_tc<BK><<<grid, 192, smem, s>>>(mx1, mx2, mw, a);
+    return cudaGetLastError();
+}
+
+cudaError_t unet_upsample2x(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s) {
+    if (c % 8) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)nb * h * w * (c / 8);
+    unet::k_upsample2x<<<nblk(n, 256), 256, 0, s>>>(x, y, nb, h, w, c);
+    return cudaGetLastError();
+}
+
 cudaError_t unet_conv3x3(const UConv &c, cudaStream_t s) {
+    using namespace unet;
+    const int cin = c.c1 + c.c2;
+    int bx, by, bimg;
+    if (!c.x1_half && cin % 32 == 0 && c.c1 % 32 == 0 && c.cout % 32 == 0 && tc_pixel_box(c.h, c.w_, bx, by, bimg)) {
+        if (c.c1 % 64 == 0 && c.c2 % 64 == 0) return launch_conv_tc<64>(c, bx, by, bimg, s);
+        return launch_conv_tc<32>(c, bx, by, bimg, s);
+    }
+    return unet_conv3x3_stage(c, s);
+}
+
+// the same convolution with cp.async staging and a synchronous pipeline (any image size,
+// upsampled input read on the fly)
+cudaError_t unet_conv3x3_stage(const UConv &c, cudaStream_t s) {
+    using namespace unet;
+    const int cin = c.c1 + c.c2;
+    const int64_t M = (int64_t)c.nb * c.h * c.w_;
+    const int64_t mtiles = (M + TBM - 1) / TBM;
+    const int bn = tc_tile_n(mtiles, c.cout);
+    if (cin % TBK || c.c1 % TBK || bn == 0) return cudaErrorInvalidValue;
+    int *err = err_word();
+    if (!err) return cudaErrorInvalidSymbol;
+    static bool tc_attr = false;
+    constexpr int kMaxSmem = TSTAGES * (TBM * TBK * 2 + 256 * TBK * 2) + 1024;
+    if (!tc_attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e != cudaSuccess) return e;
+        tc_attr = true;
+    }
+    ConvArgs a{};
+    a.x1 = c.x1; a.x2 = c.x2; a.c1 = c.c1; a.c2 = c.c2; a.x1_half = c.x1_half;
+    a.w = c.w; a.bias = c.bias; a.nb = c.nb; a.h = c.h; a.wd = c.w_; a.cout = c.cout; a.relu = c.relu; a.y = c.y;
+    a.g1 = c.g1; a.g2 = c.g2; a.m1 = c.m1; a.m2 = c.m2; a.c1o = c.c1o; a.m1_half = c.m1_half;
+    const int tcols = bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
+    const int smem = TSTAGES * (TBM * TBK * 2 + bn * TBK * 2) + 1024;
+    k_conv3x3_tc<<<dim3((unsigned)mtiles, (unsigned)(c.cout / bn)), 128, smem, s>>>(a, bn, tcols, err);
+    return cudaGetLastError();
+}
+
+cudaError_t unet_conv3x3_mma(const UConv &c, cudaStream_t s) {
     using namespace unet;
     static bool attr = false;
     const int smem = CSTAGES * (CBM + CBN) * CBK * 2;
