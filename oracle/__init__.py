@@ -15,6 +15,8 @@ Modules and what they follow:
   wu       Wu's two-point resistance of a uniform free-boundary mesh (Eq. 3)
   reduced  the paper's reduced TSV system (Eq. 6-12) and its transformed,
            pair-independent form (Eq. 13-15)
+  pairs    pairwise R (Eq. 2 / Eq. 4 on the grounded network) and IR drop
+           G^-1 I (Eq. 1), exact and as same-seed JL estimates from Z
 
 Every function here is pinned by a test in tests/test_oracle_pins.py against a
 closed form, an identity or brute force; none is "parity unpinned".

@@ -3,7 +3,8 @@
 Each test fixes the oracle to something other than itself: textbook networks,
 Wu's closed form (Eq. 3), the paper's reduced TSV system (Eq. 10 and Eq. 13-15),
 Foster's theorem, Rayleigh monotonicity, the Eq. 2 pseudo-inverse route, the
-Eq. 4 Green's-function identity, published SplitMix64 outputs and JL statistics.
+Eq. 4 Green's-function identity, Kirchhoff's current law, published SplitMix64
+outputs and JL statistics.
 """
 import json
 import os
@@ -11,7 +12,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import exact, network, reduced, sketch, wu
+from oracle import exact, network, pairs, reduced, sketch, wu
 from paper_2607_05818_gb300 import instances as I
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -226,6 +227,122 @@ def test_P11_eq4_green_function_identity():
             Rbk = exact.pair_reff_pinv(L, b, k)
             Rjk = exact.pair_reff_pinv(L, j, k) if j != k else 0.0
             assert Gb_inv[jj, kk] == pytest.approx(0.5 * (Rbj + Rbk - Rjk), rel=1e-9)
+
+
+# ------------------------------------------------------- pairwise R and IR drop
+
+def test_P12_pairs_and_drop_on_a_chain():
+    """1 x L chain with one pad of resistance 1/g at x = 0: R(u, v) is the sum of the segments
+    between u and v (the only path), and a current I drawn at x_l lowers node x by
+    I (1/g + sum of the segments below min(x, x_l))."""
+    rng = np.random.default_rng(41)
+    L = 13
+    rx = rng.uniform(0.01, 0.3, (1, 1, L - 1))
+    g = 25.0
+    inst = I.from_resistances(rx, np.zeros((1, 0, L)), pads=[(0, 0, 0, 1 / g)])
+    cum = np.concatenate([[0.0], np.cumsum(rx[0, 0])])
+    Rp = pairs.pair_reff_exact(inst, np.arange(L), np.arange(L))
+    np.testing.assert_allclose(Rp, np.abs(cum[:, None] - cum[None, :]), rtol=1e-12, atol=1e-14)
+    loads = [4, 9]
+    cur = np.array([[2.0, 0.5], [1.0, -0.25]])  # two load scenarios
+    drop = pairs.ir_drop_exact(inst, loads, cur)
+    x = np.arange(L)
+    for s in range(2):
+        want = sum(cur[j, s] * (1 / g + cum[np.minimum(x, xl)]) for j, xl in enumerate(loads))
+        np.testing.assert_allclose(drop[:, s], want, rtol=1e-12)
+
+
+def test_P13_pair_reff_is_eq2_on_the_laplacian_with_supply():
+    """Eq. 2 taken literally on the (n+1)-node Laplacian, paths through the supply included."""
+    rng = np.random.default_rng(42)
+    for _ in range(3):
+        inst = I.random_small(rng, T=2, W=3, H=3, n_pads=2)
+        L = network.laplacian_with_supply(inst)
+        us, vs = rng.permutation(inst.n)[:4], rng.permutation(inst.n)[:5]
+        Rp = pairs.pair_reff_exact(inst, us, vs)
+        for a, u in enumerate(us):
+            for b, v in enumerate(vs):
+                want = 0.0 if u == v else exact.pair_reff_pinv(L, int(u), int(v))
+                assert Rp[a, b] == pytest.approx(want, rel=1e-10, abs=1e-14)
+
+
+def test_P14_drop_obeys_kcl_superposition_and_eq4():
+    """G drop = I at every node (Kirchhoff's current law); drops of several loads add; and for a
+    unit current at l, drop_i = (G^-1)_il = (R_i + R_l - R(i, l)) / 2 (Eq. 4 with the supply as
+    the grounded node), from the map and the Eq. 2 pairwise resistance."""
+    rng = np.random.default_rng(43)
+    inst = I.random_small(rng, T=3, W=5, H=4, n_tsv=6, n_pads=2)
+    loads = rng.choice(inst.n, 7, replace=False)
+    cur = rng.uniform(-1.0, 2.0, (7, 3))
+    drop = pairs.ir_drop_exact(inst, loads, cur)
+    G = network.conductance_matrix(inst, dense=True)
+    b = np.zeros((inst.n, 3))
+    b[loads] = cur
+    np.testing.assert_allclose(G @ drop, b, rtol=0, atol=1e-10)
+    parts = sum(pairs.ir_drop_exact(inst, [l], cur[j:j + 1]) for j, l in enumerate(loads))
+    np.testing.assert_allclose(parts, drop, rtol=1e-11)
+    Rs = exact.reff_dense(inst)
+    Lp = network.laplacian_with_supply(inst)
+    l = int(loads[0])
+    unit = pairs.ir_drop_exact(inst, [l], [1.0])[:, 0]
+    for i in range(inst.n):
+        Ril = 0.0 if i == l else exact.pair_reff_pinv(Lp, i, l)
+        assert unit[i] == pytest.approx(0.5 * (Rs[i] + Rs[l] - Ril), rel=1e-9)
+
+
+def test_P15_jl_pairs_and_drop_statistics_and_same_seed_identities():
+    """Over seeds the JL pair and drop estimates average to the exact values; for one seed,
+    R_JL(u, v) = R_JL,u + R_JL,v - 2 drop_JL(u; unit current at v) and drop_JL(u; unit at u) =
+    R_JL,u, tying both to the R map of the same sketch."""
+    rng = np.random.default_rng(44)
+    inst = I.random_small(rng, T=2, W=4, H=3, n_tsv=3, n_pads=2)
+    us, vs = np.array([0, 5, 13, 22]), np.array([1, 7, 13, 20, 23])
+    loads, cur = np.array([3, 17, 22]), np.array([1.0, 0.5, 2.0])
+    Rex = pairs.pair_reff_exact(inst, us, vs)
+    Dex = pairs.ir_drop_exact(inst, loads, cur)[:, 0]
+    fl = network.floating_mask(inst)
+    k, S = 32, 256
+    Rs, Ds = [], []
+    for s in range(S):
+        Rmap, Z = sketch.reff_jl_dense(inst, k, 900 + s)
+        Rs.append(pairs.pair_reff_jl(Z, fl, us, vs))
+        Ds.append(pairs.ir_drop_jl(Z, fl, loads, cur)[:, 0])
+        if s == 0:
+            for a, u in enumerate(us):
+                for b, v in enumerate(vs):
+                    unit_v = pairs.ir_drop_jl(Z, fl, [v], [1.0])[u, 0]
+                    assert Rs[0][a, b] == pytest.approx(Rmap[u] + Rmap[v] - 2 * unit_v, rel=1e-10, abs=1e-13)
+            for u in us:
+                assert pairs.ir_drop_jl(Z, fl, [u], [1.0])[u, 0] == pytest.approx(Rmap[u], rel=1e-12)
+    Rs, Ds = np.stack(Rs), np.stack(Ds)
+    off = us[:, None] != vs[None, :]
+    assert np.all(Rs[:, ~off] == 0.0)
+    assert np.all(np.abs(Rs.mean(0) - Rex)[off] <= 4 * (Rs.std(0) / np.sqrt(S))[off])
+    assert np.all(np.abs(Ds.mean(0) - Dex) <= 4 * Ds.std(0) / np.sqrt(S) + 1e-15)
+
+
+def test_pairs_and_drop_with_floating_nodes():
+    """Pairs touching a floating node and drops at one are +inf; currents at floating nodes are
+    ignored (no path to the supply); the rest equals the network without those currents."""
+    rng = np.random.default_rng(45)
+    for _ in range(20):
+        inst = I.random_small(rng, T=1, W=6, H=5, n_pads=1, open_frac=0.4)
+        fl = network.floating_mask(inst)
+        if fl.any() and (~fl).sum() >= 3:
+            break
+    assert fl.any()
+    us, vs = np.arange(inst.n), np.arange(inst.n)
+    Rp = pairs.pair_reff_exact(inst, us, vs)
+    assert np.all(np.isinf(Rp[fl, :])) and np.all(np.isinf(Rp[:, fl]))
+    assert np.all(np.isfinite(Rp[np.ix_(~fl, ~fl)]))
+    good, bad = np.flatnonzero(~fl)[:2], np.flatnonzero(fl)[:1]
+    drop = pairs.ir_drop_exact(inst, np.concatenate([good, bad]), [1.0, 2.0, 5.0])[:, 0]
+    ref = pairs.ir_drop_exact(inst, good, [1.0, 2.0])[:, 0]
+    assert np.all(np.isinf(drop[fl]))
+    np.testing.assert_allclose(drop[~fl], ref[~fl], rtol=1e-13)
+    _, Z = sketch.reff_jl_dense(inst, 16, 3)
+    dj = pairs.ir_drop_jl(Z, fl, np.concatenate([good, bad]), [1.0, 2.0, 5.0])[:, 0]
+    assert np.all(np.isinf(dj[fl])) and np.all(np.isfinite(dj[~fl]))
 
 
 # --------------------------------------------------------------------- sketch
