@@ -324,7 +324,7 @@ def run_surrogate(args, rank, world, local_rank):
     nb = 32
     pred = torch.empty((args.sur_screen, W, W, T), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    fwd_launches = 5 * L - 2
+    fwd_launches = 6 * L - 3  # 2L convolutions, L-1 pools, L-1 upsamplings, 2(L-1) decoder convolutions, head
 
     def step(verify=True):
         """(forward ms by events, forward+rank s, verify s, flagged ids, verified R, stats)."""
@@ -417,6 +417,178 @@ def run_surrogate(args, rank, world, local_rank):
         "setup": {"maps_s": t_maps, "label_solve_s": t_label, "train_s": t_train,
                   "train_loss_first_last": [hist[0], hist[-1]]},
         "gpu_launches": launches, "clocks": clk.summary(),
+    }
+
+
+def fp32_alu_peak(sm_mhz=None):
+    """FP32 CUDA-core peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock
+    (the measured median under load when given, else the 2,070 MHz maximum)."""
+    mhz = sm_mhz or 2070.0
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_pairs(args, rank, world, local_rank):
+    """Bump-to-load pair resistances and an IR-drop map from one solved sketch of the 4x512x512
+    network (FP32 form, k = 256): the 1,024 pads as bumps x 10,000 seeded load nodes on the top
+    tier (the paper's bump-load setting), and the drop of every node under 4 load-current
+    scenarios drawn at the same loads.  Setup (sketch + solve) is untimed; one step is
+    er_pair_reff + er_ir_drop."""
+    import torch
+    from paper_2607_05818_gb300 import er
+    from paper_2607_05818_gb300 import instances as I
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    inst = I.precision_4x512(seed=I.BASE_SEED + 1 + 1000 * rank)
+    k, seed, n_loads, S = args.k, int(inst.meta.get("seed", 1)), 10000, 4
+    g = er.grid_create(inst)
+    Yt = torch.empty((inst.n, k), dtype=torch.float32, device=dev)
+    Z = torch.empty_like(Yt)
+    er.sketch(g, k, seed, "fp32", Yt)
+    er.solve(g, Yt, Z, k, "fp32")
+    del Yt
+    bumps = (inst.pad_tier.astype(np.int64) * inst.H + inst.pad_y) * inst.W + inst.pad_x
+    rng = np.random.default_rng(5 + rank)
+    top = (inst.T - 1) * inst.W * inst.H
+    loads = top + rng.choice(inst.W * inst.H, n_loads, replace=False)
+    cur = rng.uniform(0.0, 1e-3, (n_loads, S))
+    Rp = torch.empty((len(bumps), n_loads), dtype=torch.float64, device=dev)
+    D = torch.empty((inst.n, S), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step():
+        a0, a1, a2 = ev(), ev(), ev()
+        a0.record(stream)
+        er.pair_reff(g, Z, k, "fp32", bumps, loads, Rp)
+        a1.record(stream)
+        er.ir_drop(g, Z, k, "fp32", loads, cur, D)
+        a2.record(stream)
+        return a0, a1, a2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = []
+    with ClockSampler(gpu_index(local_rank)) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(args.steps):
+            evs.append(step())
+        e1.record(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+    npairs = len(bumps) * n_loads
+    n_job, s_max = combine_ranks(npairs, e0.elapsed_time(e1) / 1e3, world, dev)
+    value = n_job * args.steps / s_max
+    pair_ms = statistics.median(a.elapsed_time(b) for a, b, _ in evs)
+    drop_ms = statistics.median(b.elapsed_time(c) for _, b, c in evs)
+    cs = clk.summary()
+    peak_alu = fp32_alu_peak(cs.get("sm_mhz") if isinstance(cs, dict) else None)
+    pair_flops = 3.0 * npairs * k  # per column: one subtraction and one FMA (2 flops)
+    drop_bytes = inst.n * k * 4 + n_loads * k * 4 + inst.n * S * 8
+    peaks = load_peaks()
+    # the oracle's definitions on a bounded sample: 64 bumps x 10,000 loads and the drop of
+    # all nodes of a 1/8 slice, on a seeded random Z of the same row length
+    cpu = None
+    if rank == 0 and world == 1:
+        rs = np.random.default_rng(9)
+        Zs = rs.standard_normal((inst.n // 8, k)) * 0.05
+        fl = np.zeros(len(Zs), dtype=bool)
+        lo = rs.choice(len(Zs), n_loads, replace=False)
+        from oracle import pairs as op
+        t0 = time.perf_counter()
+        op.pair_reff_jl(Zs, fl, lo[:64], lo)
+        t1 = time.perf_counter()
+        op.ir_drop_jl(Zs, fl, lo, cur)
+        t2 = time.perf_counter()
+        cpu = {"value": 64 * n_loads / (t1 - t0), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle.pairs.pair_reff_jl on 64 x {n_loads} pairs ({t1 - t0:.2f} s) and ir_drop_jl "
+                         f"of {len(Zs)} nodes x {S} scenarios ({t2 - t1:.2f} s, "
+                         f"{len(Zs) / (t2 - t1):.3g} nodes/s), random Z with k = {k}"}
+    return {
+        "metric": "bump-load pair effective resistances per second from the solved sketch (FP32 Z)",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * s_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (differences) + f64 (sums)", "data": "synthetic",
+        "config": {"workload": "pairs_4x512x512", "k": k, "bumps": int(len(bumps)), "loads": n_loads,
+                   "drop_scenarios": S, "nodes": inst.n,
+                   "l2": "Z is 1 GiB, larger than L2; the pair kernel re-reads its 11 MB of rows from L2"},
+        "roofline": {"kernel": "k_pair_reff<float>", "bound": "alu", "achieved": pair_flops / (pair_ms / 1e3) / 1e12,
+                     "peak": peak_alu, "unit": "TFLOP/s", "frac": pair_flops / (pair_ms / 1e3) / 1e12 / peak_alu,
+                     "traffic": None, "avg_launch_ms": pair_ms, "flops_per_launch": pair_flops,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x median SM clock"},
+        "roofline_other": [{"kernel": "er_ir_drop (k_drop_partial + k_drop_fold + k_drop_apply)", "bound": "hbm",
+                            "achieved": drop_bytes / (drop_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": drop_bytes / (drop_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                            "avg_call_ms": drop_ms, "algorithmic_bytes_per_call": drop_bytes,
+                            "peak_source": peaks["source"] + " hbm_gbs"}],
+        "ir_drop": {"value": inst.n / (drop_ms / 1e3), "unit": "nodes/s", "scenarios": S},
+        "cpu_baseline": cpu,
+        "gpu_launches": 4 * args.steps, "clocks": cs,
+    }
+
+
+def run_unet_forward(args, rank, world, local_rank):
+    """The surrogate's forward alone: the 6-level, 32-base-channel BF16 U-Net (random He
+    weights; the arithmetic does not depend on them) over --sur-screen random 4x256x256
+    candidate maps in batches of 32, timed with CUDA events.  Isolates the tcgen05 convolution
+    kernels from training and verification."""
+    import torch
+    from paper_2607_05818_gb300 import er
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    T, W, L, C, in_ch, nb = 4, 256, 6, 32, 32, 32
+    model = er.Surrogate(in_ch=in_ch, out_ch=T, levels=L, base=C, H=W, W=W, seed=3 + rank)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11 + rank)
+    maps = torch.rand((args.sur_screen, W, W, in_ch), generator=gen, device=dev).to(torch.bfloat16)
+    out = torch.empty((args.sur_screen, W, W, T), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for lo in range(0, args.sur_screen, nb):
+            b = min(nb, args.sur_screen - lo)
+            model.infer(maps[lo:lo + b], b, out[lo:lo + b])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index(local_rank)) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+    n_job, s_max = combine_ranks(args.sur_screen * T * W * W, e0.elapsed_time(e1) / 1e3, world, dev)
+    value = n_job * args.steps / s_max
+    flops = unet_conv_flops(L, C, in_ch, W, W) * args.sur_screen * args.steps
+    ach = flops / (e0.elapsed_time(e1) / 1e3) / 1e12
+    pk = load_peaks()
+    return {
+        "metric": "surrogate forward R_eff-map nodes/s (BF16 U-Net on tcgen05)", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": "unet_forward_4x256x256", "candidates": args.sur_screen, "batch": nb,
+                   "unet": {"levels": L, "base": C, "in_ch": in_ch, "params": model.num_params()},
+                   "l2": f"inputs larger than L2 ({args.sur_screen * W * W * in_ch * 2 / 1e9:.1f} GB of maps)"},
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / pk["bf16_tflops"], "traffic": None,
+                     "kernel": "whole U-Net forward (3x3 conv flops / forward time; pool, upsample and head included)",
+                     "peak_source": pk["source"] + " bf16_tflops (burst)"},
+        "gpu_launches": (6 * L - 3) * ((args.sur_screen + nb - 1) // nb) * args.steps, "clocks": clk.summary(),
     }
 
 
@@ -590,8 +762,10 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload.startswith("batch_candidates") or args.workload.startswith("surrogate"):
-        run = run_batch if args.workload.startswith("batch_candidates") else run_surrogate
+    special = {"batch_candidates": run_batch, "surrogate": run_surrogate, "pairs": run_pairs,
+               "unet_forward": run_unet_forward}
+    run = next((f for pre, f in special.items() if args.workload.startswith(pre)), None)
+    if run is not None:
         line = run(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line))

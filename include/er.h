@@ -262,6 +262,32 @@ er_status er_surrogate_train_step(er_surrogate *s, const void *maps, const float
 er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R,
                       void *stream);
 
+/* ---- pairwise effective resistance and IR drop from the solved sketch ------------------ */
+
+/* Bump-to-load style pair matrix: Rp[a*nv + b] = ||Z_{u[a]} - Z_{v[b]}||^2, the same-seed JL
+ * estimate of R(u, v) = (e_u - e_v)^T G^-1 (e_u - e_v), the effective resistance between two
+ * network nodes (paper Sec. II-B, Eq. 2; with the supply grounded, Eq. 4 gives
+ * (G^-1)_uv = (R_u + R_v - R(u, v)) / 2).  Paths through the supply count: pads are joined
+ * through it.  Z is the er_solve output [n][k] (FP64 or FP32 by `prec`, device); u [m] and
+ * v [nv] are HOST arrays of node ids (validated, then copied); Rp is a device array
+ * [m][nv] (FP64).  Pairs touching a floating node get +inf; u == v gives 0.  FP32 Z:
+ * differences and squares in FP32 over runs of 32 columns, run sums in FP64.  Uses a
+ * scratch buffer cached on the grid (grown with cudaMalloc when needed).  Synchronises
+ * `stream`.  m or nv = 0 is a no-op. */
+er_status er_pair_reff(er_grid *g, const void *Z, int32_t k, er_precision prec, const int64_t *u, int32_t m,
+                       const int64_t *v, int32_t nv, double *Rp, void *stream);
+
+/* IR drop under S load scenarios (paper Sec. II-A, Eq. 1: G V = I with the supply as
+ * reference): drop[i*S + s] = Z_i . w_s with w_s = sum_l I[l*S + s] Z_{loads[l]}, the same-seed
+ * JL estimate of (G^-1 I_s)_i, the voltage drop at node i when current I[l*S + s] (amperes,
+ * positive = drawn from the network) leaves at node loads[l].  loads [n_loads] and
+ * I [n_loads][S] are HOST arrays (validated, copied); drop is a device array [n][S] (FP64).
+ * 1 <= S <= 8 and S*k <= 8192.  Currents at floating nodes have zero Z rows and add nothing;
+ * the drop at a floating node is +inf.  The fold over loads is deterministic (fixed order).
+ * Uses the grid's cached scratch buffer; synchronises `stream`. */
+er_status er_ir_drop(er_grid *g, const void *Z, int32_t k, er_precision prec, const int64_t *loads, const double *I,
+                     int64_t n_loads, int32_t S, double *drop, void *stream);
+
 /* One call from host data to the host R map: create the grid, sketch, solve, map,
  * copy R [n] (FP64) back to R_host, destroy.  Device memory comes from a cached
  * per-device pool (er_release_pool frees it).  stats may be NULL. */

@@ -212,7 +212,7 @@ bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 void free_grid_arrays(er::GridDev &d) {
     void *ptrs[] = {d.cE64, d.cS64, d.cE32, d.cS32, d.dinvs, d.tsv_ptr, d.tsv_nbr, d.tsv_c64, d.tsv_c32,
                     d.gxr, d.gyr, d.tsv_eid, d.tsv_sgn, d.tsv_g, d.pad_ptr, d.pad_eid, d.pad_g, d.floating,
-                    d.coef32, d.tsv_g32};
+                    d.coef32, d.tsv_g32, d.aux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }

@@ -72,6 +72,8 @@ struct GridDev {
     double *pad_g = nullptr;
     uint8_t *floating = nullptr;
     struct Workspace *ws = nullptr;         // cached solve workspace (er_pcg.cu)
+    void *aux = nullptr;                    // pairwise R / IR drop scratch (er_pairs.cu)
+    size_t aux_bytes = 0;
 };
 
 // rows: y rows per CTA (0 = default 64, clipped to H); order: 0 default, 1 column blocks
@@ -80,6 +82,9 @@ Tiling make_tiling(const GridDev &g, int k, int elem_bytes, int rows = 0, int or
 
 // er_pcg.cu
 void free_workspace(GridDev *g);
+
+// er_grid.cu: k a positive multiple of 4, p non-NULL and 16-byte aligned
+er_status check_nk(const er_grid *g, int32_t k, const void *p, const char *name);
 
 }  // namespace er
 

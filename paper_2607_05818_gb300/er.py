@@ -97,6 +97,10 @@ _sig = {
                               c_int32, c_uint64, c_int32, POINTER(er_solve_opts), c_void_p,
                               POINTER(er_solve_stats), c_void_p]),
     "er_release_pool": (_S, []),
+    "er_pair_reff": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                          c_void_p]),
+    "er_ir_drop": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
+                        c_void_p]),
     "er_surrogate_create": (_S, [POINTER(er_unet_shape), c_uint64, POINTER(c_void_p)]),
     "er_surrogate_destroy": (_S, [c_void_p]),
     "er_surrogate_num_params": (_S, [c_void_p, POINTER(c_int64)]),
@@ -256,6 +260,25 @@ def solve_noalloc(grid: Grid, Yt, Z, k: int, opts: er_solve_opts | None = None, 
 def reff_map(grid: Grid, Z, k: int, prec, R, stream=None):
     return _check(_lib.er_reff_map(grid.handle, _ptr(Z), k, PRECISIONS[prec], _ptr(R), _stream(stream)),
                   "er_reff_map")
+
+
+def pair_reff(grid: Grid, Z, k: int, prec, u, v, Rp, stream=None):
+    """Rp[a, b] = ||Z_u[a] - Z_v[b]||^2 (device FP64 [len(u)][len(v)]); u, v: host node ids."""
+    ua = np.ascontiguousarray(u, dtype=np.int64)
+    va = np.ascontiguousarray(v, dtype=np.int64)
+    return _check(_lib.er_pair_reff(grid.handle, _ptr(Z), k, PRECISIONS[prec], ua.ctypes.data, len(ua),
+                                    va.ctypes.data, len(va), _ptr(Rp), _stream(stream)), "er_pair_reff")
+
+
+def ir_drop(grid: Grid, Z, k: int, prec, loads, currents, drop, stream=None):
+    """drop (device FP64 [n][S]) = Z (Z^T I) for host loads [L] and currents [L] or [L][S]."""
+    la = np.ascontiguousarray(loads, dtype=np.int64)
+    cur = np.asarray(currents, dtype=np.float64)
+    cur = np.ascontiguousarray(cur[:, None] if cur.ndim == 1 else cur)
+    if cur.shape[0] != len(la):
+        raise ValueError("currents must have one row per load")
+    return _check(_lib.er_ir_drop(grid.handle, _ptr(Z), k, PRECISIONS[prec], la.ctypes.data, cur.ctypes.data,
+                                  len(la), cur.shape[1], _ptr(drop), _stream(stream)), "er_ir_drop")
 
 
 def batch_solve(grids, k: int, seed: int, R_out, prec="fp32", opts: er_solve_opts | None = None,

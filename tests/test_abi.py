@@ -109,5 +109,7 @@ def test_host_validation_without_gpu(er):
     assert er._lib.er_sketch(None, 128, 1, 0, 16, None) == er.ER_ERR_INVALID_ARG
     assert er._lib.er_reff_map(None, 16, 128, 0, 16, None) == er.ER_ERR_INVALID_ARG
     assert er._lib.er_solve(None, 16, 32, 128, 0, None, None, None) == er.ER_ERR_INVALID_ARG
+    assert er._lib.er_pair_reff(None, 16, 128, 0, None, 1, None, 1, 16, None) == er.ER_ERR_INVALID_ARG
+    assert er._lib.er_ir_drop(None, 16, 128, 0, None, None, 1, 1, 16, None) == er.ER_ERR_INVALID_ARG
     assert er._lib.er_grid_destroy(None) == er.ER_OK
     assert er.status_str(er.ER_WARN_FLOATING) == "ER_WARN_FLOATING"
