@@ -271,7 +271,7 @@ er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, d
  * through it.  Z is the er_solve output [n][k] (FP64 or FP32 by `prec`, device); u [m] and
  * v [nv] are HOST arrays of node ids (validated, then copied); Rp is a device array
  * [m][nv] (FP64).  Pairs touching a floating node get +inf; u == v gives 0.  FP32 Z:
- * differences and squares in FP32 over runs of 32 columns, run sums in FP64.  Uses a
+ * differences and squares in FP32 over runs of 64 columns, run sums in FP64.  Uses a
  * scratch buffer cached on the grid (grown with cudaMalloc when needed).  Synchronises
  * `stream`.  m or nv = 0 is a no-op. */
 er_status er_pair_reff(er_grid *g, const void *Z, int32_t k, er_precision prec, const int64_t *u, int32_t m,
@@ -283,10 +283,53 @@ er_status er_pair_reff(er_grid *g, const void *Z, int32_t k, er_precision prec, 
  * positive = drawn from the network) leaves at node loads[l].  loads [n_loads] and
  * I [n_loads][S] are HOST arrays (validated, copied); drop is a device array [n][S] (FP64).
  * 1 <= S <= 8 and S*k <= 8192.  Currents at floating nodes have zero Z rows and add nothing;
- * the drop at a floating node is +inf.  The fold over loads is deterministic (fixed order).
+ * the drop at a floating node is +inf.  The fold over loads is deterministic (fixed order)
+ * and runs in FP64; the final dot products run in the precision of Z (FP32 Z: rounding of
+ * a few units of 1e-7 of ||Z_i|| ||w_s||, the level of Z's own FP32 rounding).
  * Uses the grid's cached scratch buffer; synchronises `stream`. */
 er_status er_ir_drop(er_grid *g, const void *Z, int32_t k, er_precision prec, const int64_t *loads, const double *I,
                      int64_t n_loads, int32_t S, double *drop, void *stream);
+
+/* ---- the paper's own bump-to-load pipeline on a uniform die stack --------------------- */
+
+/* A stack of d uniform dies (paper Sec. III-A/B, notation table): die i is an M x N mesh
+ * whose x-directed segments have resistance r[i] and y-directed segments s[i] (ohms); p TSV
+ * columns at (tsv_xy[2k], tsv_xy[2k+1]) join every pair of adjacent dies, segment k between
+ * die i and die i+1 having resistance Rt[i*p + k].  There is no supply: the quantity is the
+ * two-terminal resistance between a bump on die 0 and a load on die d-1. */
+typedef struct {
+    int32_t M, N;          /* mesh nodes along x and y (every die) */
+    int32_t d;             /* dies, 2..64 */
+    int32_t p;             /* TSV columns, >= 1 */
+    const double *r;       /* [d] */
+    const double *s;       /* [d] */
+    const int32_t *tsv_xy; /* [p][2] */
+    const double *Rt;      /* [d-1][p] */
+} er_stack;
+
+typedef struct {
+    int32_t n_system;   /* order of the reduced system, (p + 1)(d - 1) */
+    int64_t wu_pairs;   /* Eq. 3 evaluations */
+    double ms_wu;       /* CUDA-event phase times: cosine tables + Wu double sums */
+    double ms_build;    /* reduced system and right-hand sides */
+    double ms_lu;       /* LU factorisation */
+    double ms_solve;    /* m + n substitutions */
+    double ms_dot;      /* m x n pair dot products */
+    double seconds;     /* host wall time of the call */
+} er_stack_stats;
+
+/* R[i*n + j] = effective resistance between bump i (bump_xy[2i], bump_xy[2i+1] on die 0)
+ * and load j (load_xy[2j], load_xy[2j+1] on die d-1), by the paper's divide-and-conquer
+ * method (Sec. III-C/D/E): intra-die resistances from Wu's closed form (Eq. 3) with the
+ * cosines from the multiple-angle recursion, the pair-independent reduced TSV system
+ * (Eq. 13), one LU factorisation, m + n substitutions (Eq. 14) and the pair dot products
+ * (Eq. 15).  FP64 throughout.  Host inputs (copied); R is a device array [m][n] (FP64).
+ * Limits: M + N <= 3200, (p + 1)(d - 1) <= 46000.  Device workspace is allocated for the
+ * call and freed before it returns; synchronises `stream`.  Returns ER_ERR_INVALID_ARG for
+ * bad sizes, positions outside the mesh, non-positive resistances or a singular reduced
+ * system.  m or n = 0 is a no-op. */
+er_status er_stack_pairs(const er_stack *st, const int32_t *bump_xy, int32_t m, const int32_t *load_xy, int32_t n,
+                         double *R, er_stack_stats *stats, void *stream);
 
 /* One call from host data to the host R map: create the grid, sketch, solve, map,
  * copy R [n] (FP64) back to R_host, destroy.  Device memory comes from a cached

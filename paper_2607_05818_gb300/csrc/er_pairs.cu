@@ -8,11 +8,11 @@
 //   R_JL(u, v) = ||Z_u - Z_v||^2,      drop_JL = Z w,  w = Z^T I.
 //
 // k_pair_reff: a CTA computes a 64 x 64 block of pairs; Z rows of its u's and v's are
-// staged through shared memory in chunks of 32 columns (transposed, so a thread's four u
-// and four v values of one column are four conflict-free loads each), and each thread
-// accumulates a 4 x 4 register block of squared differences.  FP32 Z: differences and
-// squares in FP32 over a chunk, chunk sums in FP64; FP64 Z: FP64 throughout.  Differences
-// are formed before squaring, so no R_u + R_v - 2 Z_u.Z_v cancellation enters.
+// staged through shared memory in chunks of 32 columns (transposed, so a thread's four
+// consecutive u and four consecutive v of one column are one vector load each), and each
+// thread accumulates a 4 x 4 register block of squared differences.  FP32 Z: differences
+// and squares in FP32 over runs of 64 columns, run sums in FP64; FP64 Z: FP64 throughout.
+// Differences are formed before squaring, so no R_u + R_v - 2 Z_u.Z_v cancellation enters.
 //
 // IR drop: k_drop_partial folds the load rows of Z into per-CTA partial sums of w (one
 // thread per column, loads in a fixed order), k_drop_fold adds the partials in CTA order
@@ -33,54 +33,54 @@ namespace {
 constexpr int kPT = 64;   // pairs tile edge
 constexpr int kKC = 32;   // columns per staged chunk
 constexpr int kDropMaxS = 8;
-constexpr int kPartBlocks = 304;  // 2 CTAs per SM on 152 SMs
+constexpr int kPartBlocks = 152;  // one CTA per SM
 
 __device__ __forceinline__ double inf64() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T *p, T (&o)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+        const double2 t0 = *reinterpret_cast<const double2 *>(p);
+        const double2 t1 = *reinterpret_cast<const double2 *>(p + 2);
+        o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_pair_reff(const T *__restrict__ Z, int k, const int64_t *__restrict__ us,
                                                    int m, const int64_t *__restrict__ vs, int nv,
                                                    const uint8_t *__restrict__ floating, double *__restrict__ out) {
-    __shared__ T su[kKC][kPT + 1];
-    __shared__ T sv[kKC][kPT + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // rows padded by 4 scalars: 16-byte aligned, so a thread's 4 consecutive u (or v) of one
+    // column are one vector load
+    __shared__ __align__(16) T su[kKC][kPT + 4];
+    __shared__ __align__(16) T sv[kKC][kPT + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // pairs (u0 + 4ty + a, v0 + 4tx + b)
     const int u0 = blockIdx.y * kPT, v0 = blockIdx.x * kPT;
     double acc[4][4];
+    T run[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0, run[a][b] = 0;
     // loader mapping: 64 rows x 32 columns per tile = 2048 scalars, 8 per thread as 2 x 4
     const int lr = threadIdx.x >> 2;        // row 0..63
     const int lc = (threadIdx.x & 3) * 8;   // column 0, 8, 16, 24 within the chunk
     const int64_t ru = u0 + lr < m ? us[u0 + lr] : -1;
     const int64_t rv = v0 + lr < nv ? vs[v0 + lr] : -1;
+    // FP32: squares summed in FP32 over runs of kRun columns, runs in FP64 (FP64 arithmetic is
+    // a small fraction of the FP32 rate, so it is kept out of the inner loop)
+    constexpr int kRun = sizeof(T) == 4 ? 64 : kKC;
     for (int c0 = 0; c0 < k; c0 += kKC) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = c0 + lc + 4 * h;  // k is a multiple of 4, so c < k covers all four
             T a4[4] = {0, 0, 0, 0}, b4[4] = {0, 0, 0, 0};
             if (c < k) {
-                if (ru >= 0) {
-                    if constexpr (sizeof(T) == 4) {
-                        const float4 t = *reinterpret_cast<const float4 *>(Z + ru * k + c);
-                        a4[0] = t.x; a4[1] = t.y; a4[2] = t.z; a4[3] = t.w;
-                    } else {
-                        const double2 t0 = *reinterpret_cast<const double2 *>(Z + ru * k + c);
-                        const double2 t1 = *reinterpret_cast<const double2 *>(Z + ru * k + c + 2);
-                        a4[0] = t0.x; a4[1] = t0.y; a4[2] = t1.x; a4[3] = t1.y;
-                    }
-                }
-                if (rv >= 0) {
-                    if constexpr (sizeof(T) == 4) {
-                        const float4 t = *reinterpret_cast<const float4 *>(Z + rv * k + c);
-                        b4[0] = t.x; b4[1] = t.y; b4[2] = t.z; b4[3] = t.w;
-                    } else {
-                        const double2 t0 = *reinterpret_cast<const double2 *>(Z + rv * k + c);
-                        const double2 t1 = *reinterpret_cast<const double2 *>(Z + rv * k + c + 2);
-                        b4[0] = t0.x; b4[1] = t0.y; b4[2] = t1.x; b4[3] = t1.y;
-                    }
-                }
+                if (ru >= 0) lds4(Z + ru * k + c, a4);
+                if (rv >= 0) lds4(Z + rv * k + c, b4);
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -89,18 +89,11 @@ __global__ void __launch_bounds__(256) k_pair_reff(const T *__restrict__ Z, int 
             }
         }
         __syncthreads();
-        T run[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) run[a][b] = 0;
 #pragma unroll 8
         for (int kk = 0; kk < kKC; ++kk) {
             T ua[4], vb[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) ua[a] = su[kk][ty + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) vb[b] = sv[kk][tx + 16 * b];
+            lds4(&su[kk][4 * ty], ua);
+            lds4(&sv[kk][4 * tx], vb);
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -109,20 +102,22 @@ __global__ void __launch_bounds__(256) k_pair_reff(const T *__restrict__ Z, int 
                     run[a][b] = fma(d, d, run[a][b]);
                 }
         }
+        if ((c0 + kKC) % kRun == 0 || c0 + kKC >= k) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += (double)run[a][b];
+                for (int b = 0; b < 4; ++b) acc[a][b] += (double)run[a][b], run[a][b] = 0;
+        }
         __syncthreads();
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int iu = u0 + ty + 16 * a;
+        const int iu = u0 + 4 * ty + a;
         if (iu >= m) continue;
         const bool fu = floating[us[iu]] != 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int iv = v0 + tx + 16 * b;
+            const int iv = v0 + 4 * tx + b;
             if (iv >= nv) continue;
             out[(int64_t)iu * nv + iv] = (fu || floating[vs[iv]]) ? inf64() : acc[a][b];
         }
@@ -158,7 +153,10 @@ __global__ void k_drop_fold(const double *__restrict__ part, int nblk, int sk, d
     w[t] = acc;
 }
 
-// drop[i][s] = sum_j Z[i][j] w[s][j]; one warp per node, w in shared memory (as T)
+// drop[i][s] = sum_j Z[i][j] w[s][j]; one warp per node, w in shared memory (as T).  The
+// accumulation runs in T: with FP32 Z its rounding stays at a few units of 1e-7 of
+// ||Z_i|| ||w_s||, the level at which the FP32 rows of Z are themselves rounded (FP64
+// arithmetic runs at a small fraction of the FP32 rate and would bound the kernel).
 template <typename T, int S>
 __global__ void __launch_bounds__(256) k_drop_apply(const T *__restrict__ Z, int64_t n, int k,
                                                     const double *__restrict__ w, const uint8_t *__restrict__ floating,
@@ -169,12 +167,12 @@ __global__ void __launch_bounds__(256) k_drop_apply(const T *__restrict__ Z, int
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    constexpr int V = 16 / sizeof(T);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const T *row = Z + i * k;
-        double tot[S];
+        T tot[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) tot[s] = 0.0;
-        constexpr int V = 16 / sizeof(T);
+        for (int s = 0; s < S; ++s) tot[s] = 0;
         for (int c0 = lane * V; c0 < k; c0 += 32 * V) {
             T z[V];
             if constexpr (sizeof(T) == 4) {
@@ -185,26 +183,23 @@ __global__ void __launch_bounds__(256) k_drop_apply(const T *__restrict__ Z, int
                 z[0] = t.x; z[1] = t.y;
             }
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                T part = 0;
+            for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int v = 0; v < V; ++v) part = fma(z[v], sw[s * k + c0 + v], part);
-                tot[s] += (double)part;
-            }
+                for (int v = 0; v < V; ++v) tot[s] = fma(z[v], sw[s * k + c0 + v], tot[s]);
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            double x = tot[s];
+            T x = tot[s];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             tot[s] = x;
         }
         if (lane < S) {
-            double x = tot[0];
+            T x = tot[0];
 #pragma unroll
             for (int s = 1; s < S; ++s)
                 if (lane == s) x = tot[s];
-            drop[i * S + lane] = floating[i] ? inf64() : x;
+            drop[i * S + lane] = floating[i] ? inf64() : (double)x;
         }
     }
 }
@@ -325,7 +320,7 @@ er_status ir_drop(er_grid *g, const void *Z, int32_t k, er_precision prec, const
     const int nsm = sm_count(d.device);
     if (nsm <= 0) return fail(ER_ERR_CUDA, "multiprocessor count");
     const int64_t Lp = std::max<int64_t>(L, 1);
-    const int nblk = (int)std::min<int64_t>(kPartBlocks, Lp);
+    const int nblk = (int)std::min<int64_t>(kPartBlocks, (Lp + 15) / 16);
     const int64_t per_blk = (Lp + nblk - 1) / nblk;
     const size_t bl = up256((size_t)Lp * 8), bi = up256((size_t)Lp * S * 8);
     const size_t bp = up256((size_t)nblk * S * k * 8), bw = up256((size_t)S * k * 8);

@@ -73,6 +73,19 @@ class er_batch_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class er_stack(ctypes.Structure):
+    _fields_ = [("M", c_int32), ("N", c_int32), ("d", c_int32), ("p", c_int32), ("r", c_void_p), ("s", c_void_p),
+                ("tsv_xy", c_void_p), ("Rt", c_void_p)]
+
+
+class er_stack_stats(ctypes.Structure):
+    _fields_ = [("n_system", c_int32), ("wu_pairs", c_int64), ("ms_wu", c_double), ("ms_build", c_double),
+                ("ms_lu", c_double), ("ms_solve", c_double), ("ms_dot", c_double), ("seconds", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class er_unet_shape(ctypes.Structure):
     _fields_ = [("in_ch", c_int32), ("out_ch", c_int32), ("levels", c_int32), ("base", c_int32), ("H", c_int32),
                 ("W", c_int32)]
@@ -111,6 +124,8 @@ _sig = {
                                c_void_p]),
     "er_surrogate_train_step": (_S, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
                                      POINTER(c_double), c_void_p]),
+    "er_stack_pairs": (_S, [POINTER(er_stack), c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                            POINTER(er_stack_stats), c_void_p]),
     "er_status_str": (ctypes.c_char_p, [c_int32]),
     "er_last_error": (ctypes.c_char_p, []),
 }
@@ -279,6 +294,23 @@ def ir_drop(grid: Grid, Z, k: int, prec, loads, currents, drop, stream=None):
         raise ValueError("currents must have one row per load")
     return _check(_lib.er_ir_drop(grid.handle, _ptr(Z), k, PRECISIONS[prec], la.ctypes.data, cur.ctypes.data,
                                   len(la), cur.shape[1], _ptr(drop), _stream(stream)), "er_ir_drop")
+
+
+def stack_pairs(M, N, r, s, tsv_xy, Rt, bumps, loads, R, stream=None):
+    """Bump-to-load effective resistances of a uniform die stack by the paper's reduced TSV
+    system.  r, s: [d]; tsv_xy: [p][2]; Rt: [d-1][p]; bumps [m][2] (die 0), loads [n][2]
+    (die d-1), host arrays; R: device FP64 [m][n].  Returns the phase statistics."""
+    r_ = np.ascontiguousarray(r, dtype=np.float64)
+    s_ = np.ascontiguousarray(s, dtype=np.float64)
+    t_ = np.ascontiguousarray(tsv_xy, dtype=np.int32).reshape(-1, 2)
+    Rt_ = np.ascontiguousarray(Rt, dtype=np.float64).reshape(len(r_) - 1, len(t_))
+    b_ = np.ascontiguousarray(bumps, dtype=np.int32).reshape(-1, 2)
+    l_ = np.ascontiguousarray(loads, dtype=np.int32).reshape(-1, 2)
+    st = er_stack(M, N, len(r_), len(t_), r_.ctypes.data, s_.ctypes.data, t_.ctypes.data, Rt_.ctypes.data)
+    stats = er_stack_stats()
+    _check(_lib.er_stack_pairs(ctypes.byref(st), b_.ctypes.data, len(b_), l_.ctypes.data, len(l_), _ptr(R),
+                               ctypes.byref(stats), _stream(stream)), "er_stack_pairs")
+    return stats.as_dict()
 
 
 def batch_solve(grids, k: int, seed: int, R_out, prec="fp32", opts: er_solve_opts | None = None,
