@@ -694,7 +694,10 @@ def run_stack(args, rank, world, local_rank):
                      "frac": wu_flops / (med["ms_wu"] / 1e3) / 1e12 / fp64_peak, "traffic": None,
                      "flops_per_call": wu_flops, "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)"},
         "cross_check": cross, "cpu_baseline": cpu,
-        "gpu_launches": None, "clocks": cs, "hbm_peak_gbs": peaks["hbm_gbs"],
+        # per call: 2 cosine tables, d x (1/lambda + Wu), C and RHS, 4 per LU panel (the last
+        # panel has no trailing update), the solves and the pair dots
+        "gpu_launches": args.steps * (2 + 2 * d + 2 + 4 * -(-stats[-1]["n_system"] // 32) - 2 + 2),
+        "clocks": cs, "hbm_peak_gbs": peaks["hbm_gbs"],
     }
 
 

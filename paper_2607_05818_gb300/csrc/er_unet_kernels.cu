@@ -1,7 +1,12 @@
 // Kernels of the BF16 U-Net surrogate (forward and backward), sm_103a.
 //
 // Tensors are NHWC (channels innermost).  3x3 convolutions are implicit GEMMs on the
-// tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
+// tensor cores with BF16 operands and FP32 accumulation.  Three kernels share the layout:
+// k_conv_tc (persistent, warp-specialised: TMA boxes -> tcgen05.mma -> TMEM -> epilogue),
+// used whenever 128 consecutive pixels form a box of the tensor and the input is stored at
+// full resolution; k_conv3x3_tc (cp.async staging, tcgen05.mma, TMEM) for other image sizes
+// and for inputs read with on-the-fly upsampling; and k_conv3x3 (mma.sync m16n8k16), kept as
+// the legacy warp-level path:
 //   forward  Y[m][co] = act(sum_k A[m][k] W[co][k] + b[co]),  m = (n, y, x), k = (ky, kx, ci)
 //   dgrad    the same kernel on dY with W' [ci][ky][kx][co] = W[co][2-ky][2-kx][ci]
 //   wgrad    dW[co][k] = sum_m dY[m][co] A[m][k]  (split over pixels, FP32 atomics)
