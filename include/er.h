@@ -290,6 +290,15 @@ er_status er_pair_reff(er_grid *g, const void *Z, int32_t k, er_precision prec, 
 er_status er_ir_drop(er_grid *g, const void *Z, int32_t k, er_precision prec, const int64_t *loads, const double *I,
                      int64_t n_loads, int32_t S, double *drop, void *stream);
 
+/* Through-bump currents (the statistic of the paper's TSV-planning study, Sec. IV-B):
+ * I_pad[idx*S + s] = g_idx * V[i*S + s] for pad idx (input order of er_grid_create) at node
+ * i, the current it carries from the ideal supply into the network when node voltages drop
+ * by V (amperes for V in volts).  V is a device array [n][S] in the precision `prec` (FP64
+ * or FP32), e.g. the er_solve result for load currents as right-hand sides (G V = I, Eq. 1;
+ * the pad currents then add up to the total load current); I_pad is a device array
+ * [n_pads][S] (FP64).  g is the pad's conductance as given.  Async on `stream`. */
+er_status er_pad_currents(er_grid *g, const void *V, int32_t S, er_precision prec, double *I_pad, void *stream);
+
 /* ---- the paper's own bump-to-load pipeline on a uniform die stack --------------------- */
 
 /* A stack of d uniform dies (paper Sec. III-A/B, notation table): die i is an M x N mesh

@@ -18,6 +18,10 @@ so the same-seed JL estimates are
     R_JL(u, v) = ||Z_u - Z_v||^2,        drop_JL = Z (Z^T I).
 Nodes without a conducting path to a pad are excluded: any pair touching one, and the
 drop at one, is +inf; currents drawn at them are ignored (their Z rows are 0).
+
+Through-bump currents (Sec. IV-B's TSV-planning statistic): a pad of conductance g at a
+node whose voltage drops by drop_i carries g * drop_i from the supply into the network;
+by Kirchhoff's current law the pad currents add up to the total load current.
 """
 from __future__ import annotations
 
@@ -87,3 +91,25 @@ def ir_drop_jl(Z, floating, loads, I):
     out = Z @ w
     out[np.asarray(floating)] = np.inf
     return out
+
+
+def pad_currents(inst, drop):
+    """(n_pads, S) current through every pad (input order): g_pad * drop at its node."""
+    n_w = inst.W * inst.H
+    node = (np.asarray(inst.pad_tier, np.int64) * inst.H + np.asarray(inst.pad_y, np.int64)) * inst.W \
+        + np.asarray(inst.pad_x, np.int64)
+    assert node.max(initial=-1) < inst.T * n_w
+    d = np.asarray(drop, np.float64)
+    d = d[:, None] if d.ndim == 1 else d
+    return np.asarray(inst.pad_g, np.float64)[:, None] * d[node]
+
+
+def bumps_for_share(currents, share=0.95):
+    """Fraction of pads that together carry `share` of the total current, largest first
+    (the statistic quoted for the band-like and uniform TSV placements)."""
+    c = np.sort(np.abs(np.asarray(currents, np.float64)))[::-1]
+    tot = c.sum()
+    if tot <= 0:
+        return 0.0
+    k = int(np.searchsorted(np.cumsum(c), share * tot - 1e-12 * tot)) + 1
+    return min(k, len(c)) / len(c)

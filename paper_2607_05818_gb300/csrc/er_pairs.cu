@@ -204,6 +204,20 @@ __global__ void __launch_bounds__(256) k_drop_apply(const T *__restrict__ Z, int
     }
 }
 
+// I_pad[idx][s] = g_pad * V[i][s] for every pad (input order idx) at node i: the current it
+// carries from the supply into the network when node i's voltage drops by V[i][s]
+template <typename T>
+__global__ void k_pad_currents(const T *__restrict__ V, int S, int64_t n, const int32_t *__restrict__ pad_ptr,
+                               const int64_t *__restrict__ pad_eid, const double *__restrict__ pad_g, int64_t base,
+                               double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t e = pad_ptr[i]; e < pad_ptr[i + 1]; ++e) {
+        const int64_t idx = pad_eid[e] - base;
+        for (int s = 0; s < S; ++s) out[idx * S + s] = pad_g[e] * (double)V[i * S + s];
+    }
+}
+
 int sm_count(int dev) {
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
@@ -343,9 +357,33 @@ er_status ir_drop(er_grid *g, const void *Z, int32_t k, er_precision prec, const
     return ER_OK;
 }
 
+er_status pad_currents(er_grid *g, const void *V, int32_t S, er_precision prec, double *Ipad, cudaStream_t s) {
+    if (!g) return fail(ER_ERR_INVALID_ARG, "grid is NULL");
+    if (prec != ER_FP64 && prec != ER_FP32_REFINE) return fail(ER_ERR_INVALID_ARG, "bad precision");
+    if (S < 1) return fail(ER_ERR_INVALID_ARG, "S must be positive");
+    if (!V || !Ipad) return fail(ER_ERR_INVALID_ARG, "V or I_pad is NULL");
+    const GridDev &d = g->d;
+    ER_CUDA(cudaSetDevice(d.device));
+    const int64_t base = d.ex_slots + d.ey_slots + d.n_tsv;
+    const unsigned blocks = (unsigned)((d.n + 255) / 256);
+    if (prec == ER_FP64)
+        k_pad_currents<double><<<blocks, 256, 0, s>>>((const double *)V, S, d.n, d.pad_ptr, d.pad_eid, d.pad_g, base,
+                                                      Ipad);
+    else
+        k_pad_currents<float><<<blocks, 256, 0, s>>>((const float *)V, S, d.n, d.pad_ptr, d.pad_eid, d.pad_g, base,
+                                                     Ipad);
+    ER_CUDA(cudaGetLastError());
+    return ER_OK;
+}
+
 }  // namespace er
 
 extern "C" {
+
+er_status er_pad_currents(er_grid *g, const void *V, int32_t S, er_precision prec, double *I_pad, void *stream) {
+    return er::pad_currents(g, V, S, prec, I_pad, (cudaStream_t)stream);
+}
+
 
 er_status er_pair_reff(er_grid *g, const void *Z, int32_t k, er_precision prec, const int64_t *u, int32_t m,
                        const int64_t *v, int32_t nv, double *Rp, void *stream) {

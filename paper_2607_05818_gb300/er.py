@@ -124,6 +124,7 @@ _sig = {
                                c_void_p]),
     "er_surrogate_train_step": (_S, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
                                      POINTER(c_double), c_void_p]),
+    "er_pad_currents": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "er_stack_pairs": (_S, [POINTER(er_stack), c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                             POINTER(er_stack_stats), c_void_p]),
     "er_status_str": (ctypes.c_char_p, [c_int32]),
@@ -294,6 +295,12 @@ def ir_drop(grid: Grid, Z, k: int, prec, loads, currents, drop, stream=None):
         raise ValueError("currents must have one row per load")
     return _check(_lib.er_ir_drop(grid.handle, _ptr(Z), k, PRECISIONS[prec], la.ctypes.data, cur.ctypes.data,
                                   len(la), cur.shape[1], _ptr(drop), _stream(stream)), "er_ir_drop")
+
+
+def pad_currents(grid: Grid, V, S: int, prec, I_pad, stream=None):
+    """I_pad (device FP64 [n_pads][S]) = g_pad * V at each pad's node; V device [n][S]."""
+    return _check(_lib.er_pad_currents(grid.handle, _ptr(V), S, PRECISIONS[prec], _ptr(I_pad), _stream(stream)),
+                  "er_pad_currents")
 
 
 def stack_pairs(M, N, r, s, tsv_xy, Rt, bumps, loads, R, stream=None):

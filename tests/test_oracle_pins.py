@@ -345,6 +345,27 @@ def test_pairs_and_drop_with_floating_nodes():
     assert np.all(np.isinf(dj[fl])) and np.all(np.isfinite(dj[~fl]))
 
 
+def test_P16_pad_currents_obey_kcl_and_divide_by_conductance():
+    """Pad currents add up to the load current (KCL with the supply); on a 1 x L chain with a
+    pad at each end the current of a load at x splits in inverse proportion to the two
+    resistances to the supply; the share statistic counts pads largest first."""
+    rng = np.random.default_rng(46)
+    inst = I.random_small(rng, T=2, W=6, H=5, n_tsv=5, n_pads=4)
+    loads = rng.choice(inst.n, 6, replace=False)
+    cur = rng.uniform(0.1, 1.0, (6, 2))
+    pc = pairs.pad_currents(inst, pairs.ir_drop_exact(inst, loads, cur))
+    np.testing.assert_allclose(pc.sum(axis=0), cur.sum(axis=0), rtol=1e-11)
+    L, r, g1, g2, x = 9, 0.1, 20.0, 50.0, 3
+    inst = I.from_resistances(np.full((1, 1, L - 1), r), np.zeros((1, 0, L)),
+                              pads=[(0, 0, 0, 1 / g1), (0, L - 1, 0, 1 / g2)])
+    pc = pairs.pad_currents(inst, pairs.ir_drop_exact(inst, [x], [1.0]))[:, 0]
+    left, right = 1 / g1 + x * r, 1 / g2 + (L - 1 - x) * r
+    np.testing.assert_allclose(pc, [right / (left + right), left / (left + right)], rtol=1e-12)
+    assert pairs.bumps_for_share([5.0, 1.0, 1.0, 1.0, 2.0], 0.95) == 1.0
+    assert pairs.bumps_for_share([90.0, 5.0, 3.0, 2.0], 0.95) == 0.5
+    assert pairs.bumps_for_share([100.0, 0.0, 0.0, 0.0], 0.95) == 0.25
+
+
 # --------------------------------------------------------------------- sketch
 
 def test_splitmix64_published_stream():
