@@ -4,7 +4,8 @@ One step = the whole hot path on one synthetic network already resident in HBM:
 JL sketch (er_sketch) + k-RHS Jacobi-PCG solve (er_solve) + R map (er_reff_map).
 Default workload: 4 tiers x 512x512 (1,048,576 nodes), k = 256, the FP32 form: FP32
 vectors and stencil, FP64-accumulated dots, an FP64 iterate with the FP64 residual
-substituted every 50 iterations (reliable updates), stopped at FP64 residual 1e-7.
+substituted every 50 iterations (reliable updates), stopped at FP64 residual 1e-7, with the
+aggregation-multigrid V-cycle as preconditioner (--precond jacobi: Jacobi-PCG).
 
 Prints one JSON line (rank 0).  N > 1 (torchrun): every rank maps its own network
 (independent seeds) with no collective on the data path; value = all ranks' nodes /
@@ -42,6 +43,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="precision_4x512x512")
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--precond", default="mg", choices=["jacobi", "mg"],
+                   help="FP32 form: Jacobi or aggregation-multigrid V-cycle preconditioner")
     p.add_argument("--k", type=int, default=256)
     p.add_argument("--tol", type=float, default=None)
     p.add_argument("--no-accuracy", action="store_true")
@@ -182,7 +185,7 @@ def gpu_index(local_rank):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("er_pcg.cu", "er_fp32.cu", "er_common.cuh", "er_internal.h"):
+    for f in ("er_pcg.cu", "er_fp32.cu", "er_mg.cu", "er_common.cuh", "er_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2607_05818_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -766,6 +769,10 @@ def run_ours(args, rank, world, local_rank):
     opts = er.default_solve_opts(prec)
     if args.tol is not None:
         opts.tol = args.tol
+    mg = prec == "fp32" and args.precond == "mg"
+    opts.precond = 1 if mg else 0
+    if mg:
+        opts.check_every = 4  # a V-cycle iteration costs ~4 stencil passes: poll sooner
     opts.profile = 1
     stream = torch.cuda.current_stream()
 
@@ -808,7 +815,17 @@ def run_ours(args, rank, world, local_rank):
     peak_note = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
     nk = inst.n * k
     coef = 16 * inst.n  # per-node coefficient words read by a stencil pass
-    if prec == "fp32":
+    if mg:
+        # (pass kind index, kernel, algorithmic bytes per launch).  Finest level: the restriction
+        # reads r and writes r_1 (n/4 rows); the post-sweep reads r and z_1 and writes z.  The
+        # coarse levels together (pass kind 5, one entry per V-cycle) move 3.5 n_l k s per level,
+        # n_l = n / 4^l for l >= 1, a factor 1/3 of the finest level's 3.5 n k s.
+        kinds = [(1, "k_mg_update", 6 * nk * es + coef),            # x, p', r, q in; x, r out
+                 (0, "k_mg_spmv", 4 * nk * es + coef),              # z, p in; p', q out
+                 (7, "k_mg_up<true> (finest level)", int(2.25 * nk * es) + coef),
+                 (6, "k_mg_down (finest level)", int(1.25 * nk * es) + coef),
+                 (5, "V-cycle on the coarse levels", int(3.5 * nk * es / 3))]
+    elif prec == "fp32":
         # (pass kind index, kernel, algorithmic bytes per launch)
         kinds = [(1, "k_tma<MODE_B>", 6 * nk * es + coef),   # odd iterations: r, p, x in; x, r, p' out
                  (4, "k_tma<MODE_B0>", 4 * nk * es + coef),  # even iterations: r, p in; r, p' out
@@ -817,8 +834,16 @@ def run_ours(args, rank, world, local_rank):
         kinds = [(0, "k_stencil<double,double,MODE_A_STORE>", 4 * nk * es + coef),
                  (1, "k_stream<double,MODE_S>", 6 * nk * es)]
     rl = []
+    n_levels = None
+    if mg:
+        n_levels = 1
+        Wl, Hl = inst.W, inst.H
+        while max(Wl, Hl) > 8:
+            Wl, Hl, n_levels = (Wl + 1) // 2, (Hl + 1) // 2, n_levels + 1
     for idx, name, nbytes in kinds:
         n_l = int(launches[idx])
+        if idx == 5:  # coarse-level launches of one V-cycle: down and up per level pair below
+            n_l = n_l // max(1, 2 * n_levels - 3)  # the finest, plus the coarsest level
         avg_ms = float(kms[idx]) / max(n_l, 1)
         ach = nbytes / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
         rl.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -826,7 +851,7 @@ def run_ours(args, rank, world, local_rank):
                    "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms, "launches": n_l,
                    "share_of_step": float(kms[idx]) / ms if ms > 0 else None, "peak_source": peak_note})
     rl.sort(key=lambda r: -(r["share_of_step"] or 0))
-    pass_names = ["A", "B", "R", "other", "B0"]
+    pass_names = ["A", "B", "R", "other", "B0", "MG", "MG_down0", "MG_up0"]
     pass_ms_per_step = {pass_names[i]: float(kms[i]) / args.steps for i in range(len(kms))}
     gpu_launches = int(launches.sum()) + 2 * args.steps  # + sketch and reff_map per step
 
@@ -867,6 +892,8 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if rank == 0:
         opts_e = er.default_solve_opts(prec)
+        opts_e.precond = opts.precond
+        opts_e.check_every = opts.check_every
         if args.tol is not None:
             opts_e.tol = opts.tol
         R_host = np.empty(inst.n)
@@ -936,6 +963,8 @@ def main():
             "dtype": "f32+f64" if args.prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "k": args.k, "precision": args.prec,
                        "nodes_per_rank": int(n_total / world),
+                       "preconditioner": "aggregation multigrid V-cycle" if (args.precond == "mg" and args.prec == "fp32")
+                       else "Jacobi",
                        "l2": "inputs larger than L2 (each [n][k] array is 1 GiB)",
                        "iterations_per_step": result["rank0_iterations"],
                        "fp64_residual_replacements_per_step": result["replacements"],

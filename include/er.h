@@ -102,6 +102,8 @@ typedef struct {
     int32_t tile_rows;     /* y rows swept by one CTA (0 = default 64; clipped to H) */
     int32_t block_order;   /* 0 default, 1 RHS column blocks of a tile adjacent in launch
                               order, 2 column blocks outermost */
+    int32_t precond;       /* 0 Jacobi (D^-1); 1 aggregation multigrid: one V-cycle per
+                              iteration (ER_FP32_REFINE only; see er_solve) */
 } er_solve_opts;
 
 /* Pass kinds counted in er_solve_stats.launches / kernel_ms. */
@@ -111,7 +113,10 @@ enum { ER_PASS_A = 0,      /* stencil pass: p' = z + beta p, q = G p', dot p'.q 
        ER_PASS_R = 2,      /* FP64 residual pass */
        ER_PASS_OTHER = 3,  /* initialisation, FP64 accumulation of x, final Z */
        ER_PASS_B0 = 4,     /* FP32 form, even iterations: update pass without x */
-       ER_N_PASS = 5 };
+       ER_PASS_MG = 5,     /* multigrid V-cycle kernels on the coarse levels (precond = 1) */
+       ER_PASS_MG_DOWN = 6,/* multigrid: pre-sweep and restriction on the finest level */
+       ER_PASS_MG_UP = 7,  /* multigrid: prolongation and post-sweep on the finest level */
+       ER_N_PASS = 8 };
 
 typedef struct {
     int32_t iterations;       /* PCG iterations run */
@@ -126,7 +131,7 @@ typedef struct {
 
 /* Default solve options: tol 1e-12 (FP64) / 1e-7 (FP32 form; the FP64 residual of the
  * FP64 iterate), maxit 20000, check_every 10, replace_every 50, use_graph 1,
- * profile 0, tile_rows 0, block_order 0. */
+ * profile 0, tile_rows 0, block_order 0, precond 0. */
 er_solve_opts er_default_solve_opts(er_precision prec);
 
 /* Build the device-resident grid: per-node couplings of the Jacobi-scaled matrix
@@ -168,8 +173,16 @@ er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, voi
  * dot products accumulated in FP64; every replace_every iterations the FP32
  * correction is added to an FP64 iterate and the residual is recomputed in FP64 and
  * substituted (reliable update, no restart); a column stops only when that FP64
- * residual meets tol.  Z is written in FP32.  The library allocates (and caches on
- * the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at
+ * residual meets tol.  Z is written in FP32.
+ * precond = 1 (FP32 form): the preconditioner is one V-cycle of an aggregation multigrid
+ * instead of D^-1.  Level l+1 aggregates 2 x 2 nodes of every tier of level l; since the
+ * Galerkin product P^T G P of a network's matrix is again a network (segments between
+ * aggregates kept, those inside dropped, TSVs and pads moved to their aggregate), every
+ * level is a grid built like er_grid_create's, down to at most 8 x 8 nodes per tier; one
+ * damped-Jacobi sweep before and after the coarse correction, damped-Jacobi sweeps on the
+ * coarsest level (a fixed symmetric operator, as CG needs).  The hierarchy is built on the
+ * first such call and cached on the grid.  A grid of at most 8 x 8 nodes per tier and 2,048
+ * nodes uses Jacobi.  The library allocates (and caches on the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at
  * maxit (Z valid, stats filled), ER_ERR_TIMEOUT if a kernel's bounded wait expired.
  * Synchronises. */
 er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec,

@@ -13,7 +13,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = ["er_grid.cu", "er_pcg.cu", "er_fp32.cu", "er_noalloc.cu", "er_batch.cu", "er_unet_kernels.cu",
-       "er_surrogate.cu", "er_pairs.cu", "er_stack.cu"]
+       "er_surrogate.cu", "er_pairs.cu", "er_stack.cu", "er_mg.cu"]
 LIB = os.path.join(HERE, "liber.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

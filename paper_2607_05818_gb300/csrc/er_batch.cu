@@ -43,6 +43,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
     er_solve_opts opt = o ? *o : er_default_solve_opts(prec);
     if (!(opt.tol > 0.0) || opt.maxit < 1 || opt.check_every < 1 || opt.replace_every < 1)
         return fail(ER_ERR_INVALID_ARG, "bad solve options");
+    if (opt.precond != 0) return fail(ER_ERR_INVALID_ARG, "the batching form uses Jacobi preconditioning (precond 0)");
     const int dev = grids[0] ? grids[0]->d.device : 0;
     for (int c = 0; c < n; ++c) {
         if (!grids[c] || !R_out[c]) return fail(ER_ERR_INVALID_ARG, "NULL grid or R_out entry");

@@ -278,6 +278,7 @@ struct Prof {
 
 void prof_begin(Workspace &w, Prof *pf, int kind);
 void prof_end(Workspace &w, Prof *pf, int kind);
+void flush_prof(Workspace &w, Prof &pf);  // after a synchronisation of w.s
 
 // One network of a batch: its tensor maps (r0, r1, p0, p1, x, x64, b, coef), its kernel
 // arguments (geometry, coefficients, scalars, partials) and its vectors.
@@ -298,6 +299,10 @@ er_status fp32_make_map(CUtensorMap *m, bool f64, const void *base, int64_t d0, 
 er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts &opt);
 er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er_precision prec,
                      const er_solve_opts &opt, er_solve_stats *stats, std::chrono::steady_clock::time_point t0);
+
+// er_mg.cu: the FP32 form with the aggregation-multigrid V-cycle as preconditioner
+er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const er_solve_opts &opt,
+                        er_solve_stats *stats, std::chrono::steady_clock::time_point t0);
 
 // er_fp32.cu: the FP32 form's passes (all asynchronous on w.s)
 er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z);

@@ -496,6 +496,7 @@ er_status er_grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *ts
 er_status er_grid_destroy(er_grid *g) {
     if (!g) return ER_OK;
     cudaSetDevice(g->d.device);
+    er::free_mg(&g->d);
     er::free_workspace(&g->d);
     er::free_grid_arrays(g->d);
     delete g;

@@ -73,6 +73,7 @@ struct GridDev {
     uint8_t *floating = nullptr;
     struct Workspace *ws = nullptr;         // cached solve workspace (er_pcg.cu)
     void *aux = nullptr;                    // pairwise R / IR drop scratch (er_pairs.cu)
+    struct MgHier *mg = nullptr;            // multigrid hierarchy of the FP32 form (er_mg.cu)
     size_t aux_bytes = 0;
 };
 
@@ -82,6 +83,14 @@ Tiling make_tiling(const GridDev &g, int k, int elem_bytes, int rows = 0, int or
 
 // er_pcg.cu
 void free_workspace(GridDev *g);
+
+// er_mg.cu
+void free_mg(GridDev *g);
+
+// er_grid.cu: grid assembly behind er_grid_create
+er_status grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv, int64_t n_tsv,
+                      const er_pad *pads, int64_t n_pads, const er_options *opt, cudaStream_t stream,
+                      er_grid **out);
 
 // er_grid.cu: k a positive multiple of 4, p non-NULL and 16-byte aligned
 er_status check_nk(const er_grid *g, int32_t k, const void *p, const char *name);

@@ -1,0 +1,858 @@
+// Aggregation-multigrid preconditioned CG for the FP32 form (sm_103a).
+//
+// Jacobi-PCG needs about a thousand iterations on 512^2-tier stacks whose upper tiers reach
+// the supply only through TSVs.  Here the preconditioner is one V-cycle of an aggregation
+// multigrid whose levels are themselves PDN networks:
+//   * level l+1 aggregates 2 x 2 nodes of every tier of level l (piecewise-constant
+//     prolongation P).  For a graph Laplacian P^T G P is again a graph Laplacian: a segment
+//     between two aggregates keeps its conductance (parallel ones add), a segment inside an
+//     aggregate vanishes, TSV segments and pads move to their aggregate.  So every coarse
+//     operator (the Galerkin product, exactly) is a grid of the same kind, built by
+//     er_grid_create from the aggregated network, and every level runs the same stencil;
+//   * V-cycle on level l with right-hand side r: z0 = w D^-1 r (one damped-Jacobi sweep
+//     from zero), r_c = P^T (r - G z0), z_c = V-cycle on level l+1, z = z0 + s P z_c, and
+//     one damped-Jacobi post-sweep z += w D^-1 (r - G z); the coarsest level (at most 8 x 8
+//     per tier) runs a fixed number of damped-Jacobi sweeps from zero.  Every step is a fixed
+//     linear map and the pre- and post-sweeps are each other's adjoints, so the V-cycle is a
+//     symmetric operator, as CG requires;
+//   * the pre-sweep and restriction are one kernel per level (a thread owns one aggregate and
+//     one group of 4 RHS columns); prolongation and post-sweep are one kernel per level; z0
+//     is never stored, it is recomputed from r.
+// The CG recursion is the FP32 form's (FP32 vectors, FP64-accumulated dots, FP64 iterate
+// with the FP64 residual substituted every replace_every iterations, and whenever every
+// column's recursive residual meets tol; a column stops only when that FP64 residual meets
+// tol, and a column whose recursion ran past its attainable accuracy restarts its search
+// direction), in four kernels per iteration: the V-cycle
+// (whose last kernel also forms r.z), p' = z + beta p with q = G p' and the energy p'.G p',
+// the update x += alpha p', r -= alpha q with r.D^-1 r, and small per-column folds that
+// sum per-CTA partials in a fixed order (results are identical from run to run).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "er_common.cuh"
+
+namespace er {
+
+namespace {
+
+constexpr float kOmega = 0.8f;    // damped-Jacobi weight of the smoother
+constexpr float kScale = 1.6f;    // over-correction of the coarse-grid correction
+constexpr int kCoarseSweeps = 40; // damped-Jacobi sweeps on the coarsest level
+constexpr int kCoarseMax = 2048;  // nodes of the coarsest level (one CTA holds them)
+constexpr int kSteps = 16;        // node steps per CTA in the streaming layout
+
+struct Lvl {  // one level's device arrays (kernel argument)
+    int T, W, H;
+    int64_t n;
+    const float4 *coef;  // {+-1/d, gE, gS, pad}; sign < 0: the node has TSV segments
+    const int32_t *tsv_ptr, *tsv_nbr;
+    const float *tsv_g;
+};
+
+// Thread layout shared by the node-by-RHS kernels: TPN threads per node (one group of 4
+// columns each), NPS nodes per step, kSteps steps per CTA; blockIdx.y picks TPN groups.
+struct Lay {
+    int KG = 0, TPN = 1, NPS = 256;
+    int64_t chunks = 0;
+    int ncb = 0;
+};
+
+Lay make_lay(int64_t n, int k) {
+    Lay l;
+    l.KG = k / 4;
+    while (l.TPN < l.KG && l.TPN < 32) l.TPN <<= 1;
+    l.NPS = 256 / l.TPN;
+    l.chunks = (n + (int64_t)l.NPS * kSteps - 1) / ((int64_t)l.NPS * kSteps);
+    l.ncb = (l.KG + l.TPN - 1) / l.TPN;
+    return l;
+}
+
+__device__ __forceinline__ float4 f4ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void f4st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 operator+(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 operator*(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+__device__ __forceinline__ float4 operator*(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 fma4(float s, float4 a, float4 c) {
+    return make_float4(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y), fmaf(s, a.z, c.z), fmaf(s, a.w, c.w));
+}
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// (G v)_i in edge form, pad v_i + sum_j g_ij (v_i - v_j), for a field given by val(j) at the
+// node (x, y) of id i (coordinates passed in: no divisions here); with energy: also
+// pad v_i^2 + gE (v_i - v_E)^2 + gS (v_i - v_S)^2 + sum_TSV g (v_i - v_j)^2 / 2, whose sum over
+// all nodes is v^T G v with every edge counted once.
+template <bool ENERGY, class F>
+__device__ __forceinline__ float4 apply_g(const Lvl &L, int i, int x, int y, float4 c, float4 vi, F val,
+                                          float4 *energy) {
+    float4 acc = c.w * vi;
+    float4 en = zero4();
+    if constexpr (ENERGY) en = c.w * (vi * vi);
+    if (c.y != 0.f) {
+        const float4 d = vi - val(i + 1);
+        acc = fma4(c.y, d, acc);
+        if constexpr (ENERGY) en = fma4(c.y, d * d, en);
+    }
+    if (x > 0) {
+        const float g = L.coef[i - 1].y;
+        if (g != 0.f) acc = fma4(g, vi - val(i - 1), acc);
+    }
+    if (c.z != 0.f) {
+        const float4 d = vi - val(i + L.W);
+        acc = fma4(c.z, d, acc);
+        if constexpr (ENERGY) en = fma4(c.z, d * d, en);
+    }
+    if (y > 0) {
+        const float g = L.coef[i - L.W].z;
+        if (g != 0.f) acc = fma4(g, vi - val(i - L.W), acc);
+    }
+    if (c.x < 0.f) {
+        const int32_t e1 = L.tsv_ptr[i + 1];
+        for (int32_t e = L.tsv_ptr[i]; e < e1; ++e) {
+            const float g = L.tsv_g[e];
+            const float4 d = vi - val(L.tsv_nbr[e]);
+            acc = fma4(g, d, acc);
+            if constexpr (ENERGY) en = fma4(0.5f * g, d * d, en);
+        }
+    }
+    if constexpr (ENERGY) *energy = en;
+    return acc;
+}
+
+// The four children (dy, dx) of aggregate J = (t Hc + Y) Wc + X of the coarse level: node
+// ids, coefficients and the thread's 4 columns of r.  ok = the child exists and is not
+// floating (a floating node is not in P and has no conducting segment to the others).
+struct Quad {
+    int i[2][2];
+    bool ok[2][2];
+    float4 c[2][2], r[2][2];
+};
+
+__device__ __forceinline__ void load_quad(const Lvl &F, const float *r, int k, int col, int t, int Y, int X,
+                                          Quad &q) {
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const int x = 2 * X + dx, y = 2 * Y + dy;
+            const bool in = x < F.W && y < F.H;
+            const int i = in ? (t * F.H + y) * F.W + x : 0;
+            q.i[dy][dx] = i;
+            q.c[dy][dx] = in ? F.coef[i] : zero4();
+            q.ok[dy][dx] = in && q.c[dy][dx].x != 0.f;
+            q.r[dy][dx] = q.ok[dy][dx] ? f4ld(r + (int64_t)i * k + col) : zero4();
+        }
+}
+
+// (G v) at child (dy, dx) of a quad whose four children hold v[2][2]; ext(j, c_j, dJ) gives
+// v at a node outside the quad, whose coefficients are c_j and whose aggregate is J + dJ.
+template <class E>
+__device__ __forceinline__ float4 quad_g(const Lvl &F, const Quad &q, const float4 (&v)[2][2], int dy, int dx, int X,
+                                         int Y, int WcHc, int Wc, E ext) {
+    const float4 c = q.c[dy][dx];
+    const int i = q.i[dy][dx];
+    const float4 vi = v[dy][dx];
+    float4 acc = c.w * vi;
+    if (c.y != 0.f) {  // east: the sibling, or the first node of aggregate X + 1
+        const float4 nb = dx == 0 ? v[dy][1] : ext(i + 1, F.coef[i + 1], 1);
+        acc = fma4(c.y, vi - nb, acc);
+    }
+    if (2 * X + dx > 0) {  // west
+        float g;
+        float4 nb;
+        if (dx == 1) {
+            g = q.c[dy][0].y;
+            nb = v[dy][0];
+        } else {
+            const float4 cw = F.coef[i - 1];
+            g = cw.y;
+            nb = g != 0.f ? ext(i - 1, cw, -1) : zero4();
+        }
+        if (g != 0.f) acc = fma4(g, vi - nb, acc);
+    }
+    if (c.z != 0.f) {  // south
+        const float4 nb = dy == 0 ? v[1][dx] : ext(i + F.W, F.coef[i + F.W], Wc);
+        acc = fma4(c.z, vi - nb, acc);
+    }
+    if (2 * Y + dy > 0) {  // north
+        float g;
+        float4 nb;
+        if (dy == 1) {
+            g = q.c[0][dx].z;
+            nb = v[0][dx];
+        } else {
+            const float4 cn = F.coef[i - F.W];
+            g = cn.z;
+            nb = g != 0.f ? ext(i - F.W, cn, -Wc) : zero4();
+        }
+        if (g != 0.f) acc = fma4(g, vi - nb, acc);
+    }
+    if (c.x < 0.f) {  // TSV segments: same (x, y), the tier above or below
+        const int32_t e1 = F.tsv_ptr[i + 1];
+        for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
+            const int j = F.tsv_nbr[e];
+            acc = fma4(F.tsv_g[e], vi - ext(j, F.coef[j], j > i ? WcHc : -WcHc), acc);
+        }
+    }
+    return acc;
+}
+
+// per-CTA column partials in a fixed order: run[4] per thread -> part[chunk][col]
+__device__ __forceinline__ void block_partials(const Lay &l, int k, int cg, bool colok, const double (&acc)[4],
+                                               double *part) {
+    __shared__ double sred[256 * 4];
+    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sred[(nl * l.TPN + cgl) * 4 + v] = colok ? acc[v] : 0.0;
+    __syncthreads();
+    if (threadIdx.x < l.TPN * 4) {
+        const int c = threadIdx.x / 4, v = threadIdx.x % 4;
+        double s = 0.0;
+        for (int q = 0; q < l.NPS; ++q) s += sred[(q * l.TPN + c) * 4 + v];
+        const int col = (blockIdx.y * l.TPN + c) * 4 + v;
+        if (col < k) part[(int64_t)blockIdx.x * k + col] = s;
+    }
+    (void)cg;
+}
+
+// ---- V-cycle kernels ----------------------------------------------------------------
+
+// restriction of the pre-smoothed residual: rc[J] = sum over the fine children i of J of
+// (r - G z0)_i with z0 = w D^-1 r (z0 is recomputed, never stored).  A thread owns one
+// aggregate and 4 columns: the children's values come from registers, only the 8 nodes
+// around the quad (and TSV partners) are read from memory.
+__global__ void __launch_bounds__(256) k_mg_down(Lvl F, Lvl C, int k, Lay l, const float *__restrict__ r,
+                                                 float *__restrict__ rc) {
+    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
+    const int cg = blockIdx.y * l.TPN + cgl;
+    if (cg >= l.KG) return;
+    const int col = cg * 4;
+    const int Wc = C.W, WcHc = C.W * C.H;
+    auto ext = [&](int j, float4 cj, int) { return (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col); };
+    const int J0 = blockIdx.x * l.NPS * kSteps + nl;
+    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    for (int J = J0; J < J1; J += l.NPS) {
+        const int X = J % Wc, Y = (J / Wc) % C.H, t = J / WcHc;
+        Quad q;
+        load_quad(F, r, k, col, t, Y, X, q);
+        float4 z0[2][2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) z0[dy][dx] = (kOmega * fabsf(q.c[dy][dx].x)) * q.r[dy][dx];
+        float4 acc = zero4();
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx)
+                if (q.ok[dy][dx]) acc = acc + (q.r[dy][dx] - quad_g(F, q, z0, dy, dx, X, Y, WcHc, Wc, ext));
+        f4st(rc + (int64_t)J * k + col, acc);
+    }
+}
+
+// prolongation, over-correction and post-sweep on a level, one thread per coarse aggregate
+// and 4 columns: v = z0 + s P zc on the four children, then z = v + w D^-1 (r - G v); with
+// DOT the CTA also writes its partials of r.z
+template <bool DOT>
+__global__ void __launch_bounds__(256) k_mg_up(Lvl F, Lvl C, int k, Lay l, const float *__restrict__ r,
+                                               const float *__restrict__ zc, float *__restrict__ z, double *part) {
+    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
+    const int cg = blockIdx.y * l.TPN + cgl;
+    const bool colok = cg < l.KG;
+    const int col = colok ? cg * 4 : 0;
+    const int Wc = C.W, WcHc = C.W * C.H;
+    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    const int J0 = blockIdx.x * l.NPS * kSteps + nl;
+    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    if (colok) {
+        for (int J = J0; J < J1; J += l.NPS) {
+            const int X = J % Wc, Y = (J / Wc) % C.H, t = J / WcHc;
+            auto ext = [&](int j, float4 cj, int dJ) {
+                return fma4(kScale, f4ld(zc + (int64_t)(J + dJ) * k + col),
+                            (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col));
+            };
+            Quad q;
+            load_quad(F, r, k, col, t, Y, X, q);
+            const float4 zcJ = f4ld(zc + (int64_t)J * k + col);
+            float4 v[2][2];
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx)
+                    v[dy][dx] = q.ok[dy][dx] ? fma4(kScale, zcJ, (kOmega * fabsf(q.c[dy][dx].x)) * q.r[dy][dx])
+                                             : zero4();
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy;
+                    if (x >= F.W || y >= F.H) continue;
+                    float4 out = zero4();
+                    if (q.ok[dy][dx]) {
+                        const float4 ri = q.r[dy][dx];
+                        out = fma4(kOmega * fabsf(q.c[dy][dx].x),
+                                   ri - quad_g(F, q, v, dy, dx, X, Y, WcHc, Wc, ext), v[dy][dx]);
+                        if constexpr (DOT) {
+                            run[0] = fmaf(ri.x, out.x, run[0]);
+                            run[1] = fmaf(ri.y, out.y, run[1]);
+                            run[2] = fmaf(ri.z, out.z, run[2]);
+                            run[3] = fmaf(ri.w, out.w, run[3]);
+                        }
+                    }
+                    f4st(z + (int64_t)q.i[dy][dx] * k + col, out);
+                }
+        }
+    }
+    if constexpr (DOT) {
+        double acc[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = (double)run[v];
+        block_partials(l, k, cg, colok, acc, part);
+    }
+}
+
+// coarsest level: kCoarseSweeps damped-Jacobi sweeps from zero, all nodes of the level in
+// one CTA per group of 4 columns (z ping-pongs in shared memory)
+__global__ void __launch_bounds__(256) k_mg_coarse(Lvl C, int k, const float *__restrict__ r, float *__restrict__ z) {
+    extern __shared__ __align__(16) float4 zsm[];  // [2][n]
+    const int col = blockIdx.x * 4;
+    const int n = (int)C.n;
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) zsm[i] = zero4();
+    __syncthreads();
+    for (int s = 0; s < kCoarseSweeps; ++s) {
+        const float4 *zin = zsm + (s & 1) * n;
+        float4 *zout = zsm + ((s + 1) & 1) * n;
+        auto val = [&](int j) { return zin[j]; };
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const float4 c = C.coef[i];
+            if (c.x == 0.f) {
+                zout[i] = zero4();
+                continue;
+            }
+            const float4 ri = f4ld(r + (int64_t)i * k + col);
+            const float4 zi = zin[i];
+            zout[i] = fma4(kOmega * fabsf(c.x),
+                           ri - apply_g<false>(C, i, i % C.W, (i / C.W) % C.H, c, zi, val, nullptr), zi);
+        }
+        __syncthreads();
+    }
+    const float4 *zf = zsm + (kCoarseSweeps & 1) * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f4st(z + (int64_t)i * k + col, zf[i]);
+}
+
+// ---- CG kernels (fine level) ----------------------------------------------------------
+
+// p' = z + beta p; q = G p'; partials of p'.G p' (edge energy)
+__global__ void __launch_bounds__(256) k_mg_spmv(Lvl F, int k, Lay l, const float *__restrict__ z,
+                                                 const float *__restrict__ p, const double *__restrict__ beta,
+                                                 float *__restrict__ p_out, float *__restrict__ q, double *part) {
+    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
+    const int cg = blockIdx.y * l.TPN + cgl;
+    const bool colok = cg < l.KG;
+    const int col = colok ? cg * 4 : 0;
+    const float4 b4 = colok ? make_float4((float)beta[col], (float)beta[col + 1], (float)beta[col + 2],
+                                          (float)beta[col + 3])
+                            : zero4();
+    auto val = [&](int j) {
+        const int64_t o = (int64_t)j * k + col;
+        return (b4 * f4ld(p + o)) + f4ld(z + o);
+    };
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    const int i0 = blockIdx.x * l.NPS * kSteps + nl;
+    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    if (colok) {
+        for (int i = i0; i < i1; i += l.NPS) {
+            const float4 c = F.coef[i];
+            float4 pv = zero4(), qv = zero4();
+            if (c.x != 0.f) {
+                pv = val(i);
+                float4 en;
+                qv = apply_g<true>(F, i, i % F.W, (i / F.W) % F.H, c, pv, val, &en);
+                run[0] += en.x; run[1] += en.y; run[2] += en.z; run[3] += en.w;
+            }
+            f4st(p_out + (int64_t)i * k + col, pv);
+            f4st(q + (int64_t)i * k + col, qv);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] = (double)run[v];
+    block_partials(l, k, cg, colok, acc, part);
+}
+
+// x += alpha p'; r -= alpha q; partials of r.D^-1 r
+__global__ void __launch_bounds__(256) k_mg_update(Lvl F, int k, Lay l, const double *__restrict__ alpha,
+                                                   const float *__restrict__ p, const float *__restrict__ q,
+                                                   float *__restrict__ x, float *__restrict__ r, double *part) {
+    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
+    const int cg = blockIdx.y * l.TPN + cgl;
+    const bool colok = cg < l.KG;
+    const int col = colok ? cg * 4 : 0;
+    const float4 a4 = colok ? make_float4((float)alpha[col], (float)alpha[col + 1], (float)alpha[col + 2],
+                                          (float)alpha[col + 3])
+                            : zero4();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    const int i0 = blockIdx.x * l.NPS * kSteps + nl;
+    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    if (colok) {
+        for (int i = i0; i < i1; i += l.NPS) {
+            const int64_t o = (int64_t)i * k + col;
+            const float4 pv = f4ld(p + o), qv = f4ld(q + o);
+            const float4 xv = f4ld(x + o) + a4 * pv;
+            const float4 rv = f4ld(r + o) - a4 * qv;
+            f4st(x + o, xv);
+            f4st(r + o, rv);
+            const float di = fabsf(F.coef[i].x);
+            run[0] = fmaf(di * rv.x, rv.x, run[0]);
+            run[1] = fmaf(di * rv.y, rv.y, run[1]);
+            run[2] = fmaf(di * rv.z, rv.z, run[2]);
+            run[3] = fmaf(di * rv.w, rv.w, run[3]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] = (double)run[v];
+    block_partials(l, k, cg, colok, acc, part);
+}
+
+// ---- per-column folds (one CTA per column, partials summed in a fixed tree order) -------
+
+enum { FOLD_ALPHA = 0, FOLD_RR = 1, FOLD_BETA = 2 };
+
+struct FoldArgs {
+    const double *part;
+    int64_t chunks;
+    int k;
+    double *alpha, *beta, *rho, *rho0;
+    double *relrec;  // recursive residual ||r||_{D^-1} / ||b||_{D^-1} per column (FOLD_RR)
+    int *active;
+    int *nunc;  // columns still above tol (FOLD_RR adds, FOLD_BETA resets)
+    double tol;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
+    __shared__ double s[256];
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t c = threadIdx.x; c < f.chunks; c += blockDim.x) acc += f.part[c * f.k + j];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double tot = s[0];
+    const bool act = f.active[j] != 0;
+    if constexpr (KIND == FOLD_ALPHA) {
+        f.alpha[j] = (act && tot > 0.0 && isfinite(tot)) ? f.rho[j] / tot : 0.0;
+    } else if constexpr (KIND == FOLD_RR) {
+        const double rel = f.rho0[j] > 0.0 ? sqrt(tot / f.rho0[j]) : 0.0;
+        f.relrec[j] = rel;
+        if (act && rel > f.tol) atomicAdd(f.nunc, 1);
+    } else {  // FOLD_BETA: rho' = r.z
+        if (j == 0) *f.nunc = 0;
+        if (act && f.rho[j] > 0.0 && tot > 0.0 && isfinite(tot)) {
+            f.beta[j] = tot / f.rho[j];
+            f.rho[j] = tot;
+        } else {
+            f.beta[j] = 0.0;
+            if (act && tot > 0.0 && isfinite(tot)) f.rho[j] = tot;
+        }
+    }
+}
+
+// after an FP64 residual replacement: freeze the columns whose FP64 residual meets tol and
+// count the rest.  A column whose recursive residual has run more than 100x below the FP64
+// one, or claims tol while the FP64 residual does not, has a stale search direction (the
+// recursion went on past its attainable accuracy): rho = 0 makes the next beta fold
+// restart it (beta = 0), as rescaling a stale direction stalls CG.
+__global__ void k_mg_freeze(int k, const double *resid, const double *relrec, double tol, int *active, double *rho,
+                            int *nact) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const double tr = resid[j], rec = relrec[j];
+    if (active[j] && (!(rec > 0.0) || rec < 1e-2 * tr || (!(rec > tol) && tr > tol))) rho[j] = 0.0;
+    if (active[j] && !(tr > tol)) active[j] = 0;
+    if (active[j]) atomicAdd(nact, 1);
+}
+
+unsigned ublocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+// ---- hierarchy ---------------------------------------------------------------------------
+
+struct MgHier {
+    int k = 0;
+    std::vector<er_grid *> grids;  // level l >= 1; grids[0] = nullptr (the fine grid)
+    std::vector<Lvl> lv;
+    std::vector<float *> r, z;     // per level [n][k]; r[0] is the CG residual (not owned)
+    float *q = nullptr;
+    double *part = nullptr;
+    int64_t part_chunks = 0;
+    int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
+    int *h_cnt = nullptr;          // pinned host copy
+};
+
+static Lvl level_of(const GridDev &d) {
+    Lvl l;
+    l.T = d.T; l.W = d.W; l.H = d.H; l.n = d.n;
+    l.coef = reinterpret_cast<const float4 *>(d.coef32);
+    l.tsv_ptr = d.tsv_ptr; l.tsv_nbr = d.tsv_nbr; l.tsv_g = d.tsv_g32;
+    return l;
+}
+
+void free_mg(GridDev *g) {
+    MgHier *h = g->mg;
+    if (!h) return;
+    for (size_t i = 1; i < h->grids.size(); ++i) er_grid_destroy(h->grids[i]);
+    for (size_t i = 1; i < h->r.size(); ++i) cudaFree(h->r[i]);
+    for (size_t i = 0; i < h->z.size(); ++i) cudaFree(h->z[i]);
+    if (h->q) cudaFree(h->q);
+    if (h->part) cudaFree(h->part);
+    if (h->cnt) cudaFree(h->cnt);
+    if (h->h_cnt) cudaFreeHost(h->h_cnt);
+    delete h;
+    g->mg = nullptr;
+}
+
+// The network of level l+1 from the device arrays of level l: aggregate 2 x 2 nodes per tier.
+static er_status coarsen(const GridDev &f, cudaStream_t s, er_grid **out) {
+    const int T = f.T, W = f.W, H = f.H;
+    const int Wc = (W + 1) / 2, Hc = (H + 1) / 2;
+    const int64_t n = f.n;
+    std::vector<double> gxr(n), gyr(n), tg;
+    std::vector<int32_t> tptr(n + 1), tnbr, pptr(n + 1);
+    std::vector<double> pg;
+    std::vector<uint8_t> fl(n);
+    ER_CUDA(cudaMemcpy(gxr.data(), f.gxr, n * sizeof(double), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(gyr.data(), f.gyr, n * sizeof(double), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(tptr.data(), f.tsv_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(pptr.data(), f.pad_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(fl.data(), f.floating, n, cudaMemcpyDeviceToHost));
+    tnbr.resize(tptr[n]);
+    tg.resize(tptr[n]);
+    pg.resize(pptr[n]);
+    if (tptr[n]) {
+        ER_CUDA(cudaMemcpy(tnbr.data(), f.tsv_nbr, tptr[n] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        ER_CUDA(cudaMemcpy(tg.data(), f.tsv_g, tptr[n] * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (pptr[n]) ER_CUDA(cudaMemcpy(pg.data(), f.pad_g, pptr[n] * sizeof(double), cudaMemcpyDeviceToHost));
+    (void)s;
+    auto id = [&](int t, int y, int x) { return ((int64_t)t * H + y) * W + x; };
+    std::vector<double> gx((size_t)T * Hc * std::max(Wc - 1, 0), 0.0), gy((size_t)T * std::max(Hc - 1, 0) * Wc, 0.0);
+    for (int t = 0; t < T; ++t)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t i = id(t, y, x);
+                if (fl[i]) continue;  // segments of floating islands join floating nodes only
+                if ((x & 1) && x + 1 < W && gxr[i] > 0.0)  // crosses from aggregate x/2 to x/2 + 1
+                    gx[((size_t)t * Hc + y / 2) * (Wc - 1) + x / 2] += gxr[i];
+                if ((y & 1) && y + 1 < H && gyr[i] > 0.0)
+                    gy[((size_t)t * (Hc - 1) + y / 2) * Wc + x / 2] += gyr[i];
+            }
+    std::vector<er_tsv> tsv;
+    std::vector<er_pad> pads;
+    for (int64_t i = 0; i < n; ++i) {
+        if (fl[i]) continue;
+        const int x = (int)(i % W), y = (int)((i / W) % H), t = (int)(i / ((int64_t)W * H));
+        for (int32_t e = tptr[i]; e < tptr[i + 1]; ++e)
+            if (tnbr[e] > i && tg[e] > 0.0) tsv.push_back({t, x / 2, y / 2, tg[e]});  // each segment once
+        for (int32_t e = pptr[i]; e < pptr[i + 1]; ++e)
+            if (pg[e] > 0.0) pads.push_back({t, x / 2, y / 2, pg[e]});
+    }
+    std::vector<er_tier> tiers(T);
+    for (int t = 0; t < T; ++t) {
+        tiers[t].W = Wc;
+        tiers[t].H = Hc;
+        tiers[t].gx = Wc > 1 ? gx.data() + (size_t)t * Hc * (Wc - 1) : nullptr;
+        tiers[t].gy = Hc > 1 ? gy.data() + (size_t)t * (Hc - 1) * Wc : nullptr;
+    }
+    er_options o{};
+    o.device = f.device;
+    const er_status st = grid_create(tiers.data(), T, tsv.data(), (int64_t)tsv.size(), pads.data(),
+                                     (int64_t)pads.size(), &o, nullptr, out);
+    return st == ER_WARN_FLOATING ? ER_OK : st;
+}
+
+static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
+    MgHier *h = g.mg;
+    if (!h) {
+        h = new MgHier();
+        g.mg = h;
+        h->grids.push_back(nullptr);
+        h->lv.push_back(level_of(g));
+        const GridDev *cur = &g;
+        while (std::max(cur->W, cur->H) > 8 || cur->n > kCoarseMax) {
+            if (cur->W <= 1 && cur->H <= 1) break;
+            er_grid *c = nullptr;
+            er_status st = coarsen(*cur, s, &c);
+            if (st != ER_OK) {
+                free_mg(&g);
+                return st;
+            }
+            h->grids.push_back(c);
+            h->lv.push_back(level_of(c->d));
+            cur = &c->d;
+        }
+        if (h->lv.back().n > kCoarseMax) {
+            free_mg(&g);
+            return fail(ER_ERR_INVALID_ARG, "multigrid: coarsest level too large (too many tiers)");
+        }
+        ER_CUDA(cudaMalloc(&h->cnt, 2 * sizeof(int)));
+        ER_CUDA(cudaMallocHost(&h->h_cnt, 2 * sizeof(int)));
+    }
+    if (h->k != k) {
+        for (size_t i = 1; i < h->r.size(); ++i) cudaFree(h->r[i]);
+        for (size_t i = 0; i < h->z.size(); ++i) cudaFree(h->z[i]);
+        if (h->q) cudaFree(h->q);
+        if (h->part) cudaFree(h->part);
+        h->r.assign(h->lv.size(), nullptr);
+        h->z.assign(h->lv.size(), nullptr);
+        h->q = nullptr;
+        h->part = nullptr;
+        h->k = 0;
+        for (size_t l = 0; l < h->lv.size(); ++l) {
+            const size_t bytes = (size_t)h->lv[l].n * k * sizeof(float);
+            if (l > 0) ER_CUDA(cudaMalloc(&h->r[l], bytes));
+            ER_CUDA(cudaMalloc(&h->z[l], bytes));
+        }
+        ER_CUDA(cudaMalloc(&h->q, (size_t)g.n * k * sizeof(float)));
+        h->part_chunks = make_lay(g.n, k).chunks;
+        ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(double)));
+        h->k = k;
+    }
+    *out = h;
+    return ER_OK;
+}
+
+// ---- the solve ---------------------------------------------------------------------------
+
+namespace {
+
+struct MgRun {
+    const GridDev *g;
+    Workspace *w;
+    MgHier *h;
+    int k;
+    double tol;
+    void *Z;
+};
+
+template <class K, class... A>
+void mg_launch(Workspace &w, Prof *pf, int kind, K kern, dim3 grid, int smem, A... args) {
+    prof_begin(w, pf, kind);
+    kern<<<grid, 256, smem, w.s>>>(args...);
+    prof_end(w, pf, kind);
+}
+
+FoldArgs fold_args(const MgRun &m, int64_t chunks) {
+    FoldArgs f;
+    f.part = m.h->part;
+    f.chunks = chunks;
+    f.k = m.k;
+    f.alpha = m.w->scal;
+    f.beta = m.w->scal + m.k;
+    f.rho = m.w->scal + 2 * m.k;
+    f.rho0 = m.w->scal + 3 * m.k;
+    f.relrec = m.w->scal + 5 * m.k;
+    f.active = m.w->ints;
+    f.nunc = m.h->cnt;
+    f.tol = m.tol;
+    return f;
+}
+
+// z[0] = V-cycle(r[0]) with the partials of r.z, then the beta fold
+void vcycle(const MgRun &m, const float *r0, Prof *pf) {
+    MgHier &h = *m.h;
+    const int L = (int)h.lv.size(), k = m.k;
+    for (int l = 0; l + 1 < L; ++l) {
+        const Lay lc = make_lay(h.lv[l + 1].n, k);
+        const float *rl = l == 0 ? r0 : h.r[l];
+        mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_down, dim3((unsigned)lc.chunks, lc.ncb), 0,
+                  h.lv[l], h.lv[l + 1], k, lc, rl, h.r[l + 1]);
+    }
+    const Lvl &C = h.lv[L - 1];
+    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_coarse, dim3((unsigned)(k / 4)), (int)(2 * C.n * sizeof(float4)), C, k,
+              (const float *)h.r[L - 1], h.z[L - 1]);
+    for (int l = L - 2; l >= 0; --l) {
+        const Lay lc = make_lay(h.lv[l + 1].n, k);  // one thread per aggregate of level l + 1
+        const float *rl = l == 0 ? r0 : h.r[l];
+        if (l == 0)
+            mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_up<true>, dim3((unsigned)lc.chunks, lc.ncb), 0, h.lv[l],
+                      h.lv[l + 1], k, lc, rl, (const float *)h.z[l + 1], h.z[l], h.part);
+        else
+            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_up<false>, dim3((unsigned)lc.chunks, lc.ncb), 0, h.lv[l],
+                      h.lv[l + 1], k, lc, rl, (const float *)h.z[l + 1], h.z[l], (double *)nullptr);
+    }
+    mg_launch(*m.w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_BETA>, dim3((unsigned)k), 0,
+              fold_args(m, make_lay(h.lv[1].n, k).chunks));
+}
+
+// one PCG iteration from the current residual w.r[0]: z = M r, beta, p' = z + beta p,
+// q = G p', alpha, x += alpha p', r -= alpha q, recursive residual norms
+int mg_iterate(const MgRun &m, int cur, Prof *pf) {
+    MgHier &h = *m.h;
+    Workspace &w = *m.w;
+    const int k = m.k;
+    float *r = (float *)w.r[0];
+    vcycle(m, r, pf);
+    const Lay lf = make_lay(m.g->n, k);
+    const dim3 grid((unsigned)lf.chunks, lf.ncb);
+    mg_launch(w, pf, ER_PASS_A, k_mg_spmv, grid, 0, h.lv[0], k, lf, (const float *)h.z[0], (const float *)w.p[cur],
+              (const double *)(w.scal + k), (float *)w.p[1 - cur], h.q, h.part);
+    mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_ALPHA>, dim3((unsigned)k), 0, fold_args(m, lf.chunks));
+    mg_launch(w, pf, ER_PASS_B, k_mg_update, grid, 0, h.lv[0], k, lf, (const double *)w.scal,
+              (const float *)w.p[1 - cur], (const float *)h.q, (float *)m.Z, r, h.part);
+    mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_RR>, dim3((unsigned)k), 0, fold_args(m, lf.chunks));
+    return 1 - cur;
+}
+
+}  // namespace
+
+er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const er_solve_opts &opt,
+                        er_solve_stats *stats, std::chrono::steady_clock::time_point t0) {
+    const int k = w.k;
+    const double tol = opt.tol;
+    MgHier *h = nullptr;
+    er_status st = get_mg(g, k, w.s, &h);
+    if (st != ER_OK) return st;
+    const Lvl &C = h->lv.back();
+    {
+        static bool attr = false;
+        if (!attr) {
+            ER_CUDA(cudaFuncSetAttribute(k_mg_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * kCoarseMax * sizeof(float4))));
+            attr = true;
+        }
+    }
+    (void)C;
+    MgRun m{&g, &w, h, k, tol, Z};
+    Prof pf;
+    pf.on = opt.profile != 0;
+    const bool use_graph = opt.use_graph && !pf.on;
+    ER_CUDA(cudaMemsetAsync(w.ints + w.k + w.til.n_colblk, 0, sizeof(int), w.s));  // error word
+    fp32_init(g, w, Yt, Z, tol, &pf);  // r = b, x = 0, p = 0, x64 = 0; rho0 = rho = b.D^-1 b; active
+    ER_CUDA(cudaGetLastError());
+
+    auto poll = [&](int *vals) -> er_status {
+        ER_CUDA(cudaMemcpyAsync(h->h_cnt, h->cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, w.s));
+        ER_CUDA(cudaMemcpyAsync(w.h_poll, w.ints + w.k + w.til.n_colblk, sizeof(int), cudaMemcpyDeviceToHost, w.s));
+        ER_CUDA(cudaStreamSynchronize(w.s));
+        flush_prof(w, pf);
+        vals[0] = h->h_cnt[0];
+        vals[1] = h->h_cnt[1];
+        vals[2] = w.h_poll[0];
+        return ER_OK;
+    };
+    // FP64 residual replacement: x64 += x, x = 0, r = b - G x64 (FP64); freeze columns at tol
+    auto replace = [&](int *n_active) -> er_status {
+        fp32_accum(g, w, Z, &pf);
+        fp32_residual(g, w, Yt, tol, 0, 0, &pf);
+        ER_CUDA(cudaMemsetAsync(h->cnt + 1, 0, sizeof(int), w.s));
+        prof_begin(w, &pf, ER_PASS_OTHER);
+        k_mg_freeze<<<ublocks(k, 128), 128, 0, w.s>>>(k, w.scal + 4 * k, w.scal + 5 * k, tol, w.ints,
+                                                       w.scal + 2 * k, h->cnt + 1);
+        prof_end(w, &pf, ER_PASS_OTHER);
+        ER_CUDA(cudaGetLastError());
+        int v[3];
+        st = poll(v);
+        if (st != ER_OK) return st;
+        *n_active = v[1];
+        return v[2] ? fail(ER_ERR_TIMEOUT, "a bounded wait on a bulk copy expired inside a solver kernel") : ER_OK;
+    };
+
+    int cur = 0, it = 0, replacements = 0, last_replace = 0, n_active = 1;
+    const int block = std::max(2, opt.check_every + (opt.check_every & 1));
+    bool done = false;
+    cudaGraphExec_t gexec = nullptr;
+    int g_parity = -1;
+    while (!done && it < opt.maxit) {
+        const int todo = std::min(block, opt.maxit - it);
+        if (use_graph && todo == block) {
+            if (!gexec || g_parity != cur) {
+                if (gexec) cudaGraphExecDestroy(gexec);
+                gexec = nullptr;
+                cudaGraph_t graph;
+                ER_CUDA(cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
+                int c = cur;
+                for (int i = 0; i < block; ++i) c = mg_iterate(m, c, nullptr);
+                ER_CUDA(cudaStreamEndCapture(w.s, &graph));
+                const cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+                g_parity = cur;
+            }
+            ER_CUDA(cudaGraphLaunch(gexec, w.s));
+            const int L = (int)h->lv.size();
+            pf.launches[ER_PASS_A] += block;
+            pf.launches[ER_PASS_B] += block;
+            pf.launches[ER_PASS_MG] += block * (2 * L - 3);
+            pf.launches[ER_PASS_MG_DOWN] += block;
+            pf.launches[ER_PASS_MG_UP] += block;
+            pf.launches[ER_PASS_OTHER] += block * 3;
+            if (block & 1) cur = 1 - cur;
+        } else {
+            for (int i = 0; i < todo; ++i) cur = mg_iterate(m, cur, &pf);
+        }
+        it += todo;
+        ER_CUDA(cudaGetLastError());
+        int v[3];
+        st = poll(v);
+        if (st != ER_OK) break;
+        if (v[2]) {
+            st = fail(ER_ERR_TIMEOUT, "a bounded wait on a bulk copy expired inside a solver kernel");
+            break;
+        }
+        if (v[0] == 0 || it - last_replace >= opt.replace_every) {
+            st = replace(&n_active);
+            ++replacements;
+            last_replace = it;
+            if (st != ER_OK) break;
+            done = n_active == 0;
+        }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (st != ER_OK) return st;
+    if (last_replace != it) {
+        st = replace(&n_active);
+        ++replacements;
+        if (st != ER_OK) return st;
+        done = n_active == 0;
+    }
+    fp32_final(g, w, Z, &pf);
+    ER_CUDA(cudaGetLastError());
+    std::vector<double> resid((size_t)k);
+    ER_CUDA(cudaMemcpyAsync(resid.data(), w.scal + 4 * k, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, w.s));
+    ER_CUDA(cudaStreamSynchronize(w.s));
+    flush_prof(w, pf);
+    int ok_cols = 0;
+    double mx = 0.0;
+    for (int j = 0; j < k; ++j) {
+        mx = std::max(mx, resid[j]);
+        ok_cols += (resid[j] <= tol);
+    }
+    if (stats) {
+        stats->iterations = it;
+        stats->sweeps = replacements;
+        stats->converged_cols = ok_cols;
+        stats->k = k;
+        stats->max_rel_residual = mx;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int i = 0; i < ER_N_PASS; ++i) {
+            stats->launches[i] = pf.launches[i];
+            stats->kernel_ms[i] = pf.ms[i];
+        }
+    }
+    if (!done)
+        return fail(ER_ERR_NOT_CONVERGED,
+                    std::to_string(n_active) + " columns above tol after " + std::to_string(it) + " iterations");
+    return ER_OK;
+}
+
+}  // namespace er

@@ -351,7 +351,7 @@ void prof_end(Workspace &w, Prof *pf, int kind) {
 }
 
 // after a stream synchronisation: fold the recorded event pairs into pf.ms
-static void flush_prof(Workspace &w, Prof &pf) {
+void flush_prof(Workspace &w, Prof &pf) {
     for (size_t i = 0; i < pf.kinds.size(); ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, w.evpool[2 * i], w.evpool[2 * i + 1]) == cudaSuccess) pf.ms[pf.kinds[i]] += ms;
@@ -428,6 +428,9 @@ er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec
         return fail(ER_ERR_INVALID_ARG, "bad solve options");
     if (opt.tile_rows < 0 || opt.block_order < 0 || opt.block_order > 2)
         return fail(ER_ERR_INVALID_ARG, "bad tile options");
+    if (opt.precond < 0 || opt.precond > 1) return fail(ER_ERR_INVALID_ARG, "precond must be 0 (Jacobi) or 1 (multigrid)");
+    if (opt.precond == 1 && prec != ER_FP32_REFINE)
+        return fail(ER_ERR_INVALID_ARG, "the multigrid preconditioner is available in the FP32 form");
     return ER_OK;
 }
 
@@ -456,7 +459,9 @@ er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision pr
     ER_CUDA(cudaStreamWaitEvent(w.s, w.ev, 0));
     std::vector<double> resid((size_t)k);
     w.h_resid = resid.data();
-    st = solve_core(g, w, Yt, Z, prec, opt, stats, t0);
+    // a grid too small to coarsen (at most 8 x 8 per tier) has a one-level hierarchy: Jacobi
+    const bool mg = opt.precond == 1 && (std::max(g.W, g.H) > 8 || g.n > 2048);
+    st = mg ? mg_solve_core(g, w, Yt, Z, opt, stats, t0) : solve_core(g, w, Yt, Z, prec, opt, stats, t0);
     w.h_resid = nullptr;
     return st;
 }
@@ -606,6 +611,7 @@ er_solve_opts er_default_solve_opts(er_precision prec) {
     o.profile = 0;
     o.tile_rows = 0;
     o.block_order = 0;
+    o.precond = 0;
     return o;
 }
 

@@ -46,13 +46,14 @@ class er_options(ctypes.Structure):
 class er_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("check_every", c_int32),
                 ("replace_every", c_int32), ("use_graph", c_int32),
-                ("profile", c_int32), ("tile_rows", c_int32), ("block_order", c_int32)]
+                ("profile", c_int32), ("tile_rows", c_int32), ("block_order", c_int32),
+                ("precond", c_int32)]
 
 
 class er_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("sweeps", c_int32), ("converged_cols", c_int32),
                 ("k", c_int32), ("max_rel_residual", c_double), ("seconds", c_double),
-                ("launches", c_int32 * 5), ("kernel_ms", c_double * 5)]
+                ("launches", c_int32 * 8), ("kernel_ms", c_double * 8)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -61,7 +62,7 @@ class er_solve_stats(ctypes.Structure):
         return d
 
 
-PASS_A, PASS_B, PASS_R, PASS_OTHER, PASS_B0 = range(5)
+PASS_A, PASS_B, PASS_R, PASS_OTHER, PASS_B0, PASS_MG, PASS_MG_DOWN, PASS_MG_UP = range(8)
 
 
 class er_batch_stats(ctypes.Structure):

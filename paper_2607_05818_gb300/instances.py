@@ -322,8 +322,15 @@ def random_small(rng, T=None, W=None, H=None, n_tsv=None, n_pads=None, open_frac
     return from_resistances(rx, ry, tsv, pads, f"rand_{T}x{W}x{H}")
 
 
+def precision_2x512(seed=BASE_SEED + 1) -> Instance:
+    """Half of the precision recipe (2 tiers x 512 x 512, 1,000 TSV columns in 20 clusters):
+    the small case on which profiler captures of the solver kernels run."""
+    return precision_4x512(seed=seed, T=2, n_tsv=1000, n_clusters=20)
+
+
 WORKLOADS = {
     "tiny_plain_2x32x32": tiny_plain,
+    "precision_2x512x512": precision_2x512,
     "precision_4x512x512": precision_4x512,
     "large_8x1024x1024": large_8x1024,
 }
