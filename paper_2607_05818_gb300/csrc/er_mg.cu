@@ -40,9 +40,10 @@ namespace {
 
 constexpr float kOmega = 0.8f;    // damped-Jacobi weight of the smoother
 constexpr float kScale = 1.6f;    // over-correction of the coarse-grid correction
-constexpr int kCoarseSweeps = 40; // damped-Jacobi sweeps on the coarsest level
-constexpr int kCoarseMax = 2048;  // nodes of the coarsest level (one CTA holds them)
-constexpr int kSteps = 16;        // node steps per CTA in the streaming layout
+constexpr int kCoarseTarget = 512;   // coarsen until a level has at most this many nodes
+constexpr int kCoarseMax = 2048;     // largest coarsest level (solved by its dense inverse)
+constexpr int kMaxSteps = 16;        // node steps per CTA in the streaming layout
+constexpr int kMinCtas = 1216;       // small levels: fewer steps, so at least 8 CTAs per SM
 
 struct Lvl {  // one level's device arrays (kernel argument)
     int T, W, H;
@@ -53,9 +54,10 @@ struct Lvl {  // one level's device arrays (kernel argument)
 };
 
 // Thread layout shared by the node-by-RHS kernels: TPN threads per node (one group of 4
-// columns each), NPS nodes per step, kSteps steps per CTA; blockIdx.y picks TPN groups.
+// columns each), NPS nodes per step, `steps` steps per CTA (fewer on small levels, which
+// would otherwise run on a handful of CTAs); blockIdx.y picks TPN groups.
 struct Lay {
-    int KG = 0, TPN = 1, NPS = 256;
+    int KG = 0, TPN = 1, NPS = 256, steps = kMaxSteps;
     int64_t chunks = 0;
     int ncb = 0;
 };
@@ -65,8 +67,10 @@ Lay make_lay(int64_t n, int k) {
     l.KG = k / 4;
     while (l.TPN < l.KG && l.TPN < 32) l.TPN <<= 1;
     l.NPS = 256 / l.TPN;
-    l.chunks = (n + (int64_t)l.NPS * kSteps - 1) / ((int64_t)l.NPS * kSteps);
     l.ncb = (l.KG + l.TPN - 1) / l.TPN;
+    const int64_t per_cta = (n + (int64_t)kMinCtas / l.ncb - 1) / std::max<int64_t>(1, kMinCtas / l.ncb);
+    l.steps = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSteps, (per_cta + l.NPS - 1) / l.NPS));
+    l.chunks = (n + (int64_t)l.NPS * l.steps - 1) / ((int64_t)l.NPS * l.steps);
     return l;
 }
 
@@ -232,8 +236,8 @@ __global__ void __launch_bounds__(256) k_mg_down(Lvl F, Lvl C, int k, Lay l, con
     const int col = cg * 4;
     const int Wc = C.W, WcHc = C.W * C.H;
     auto ext = [&](int j, float4 cj, int) { return (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col); };
-    const int J0 = blockIdx.x * l.NPS * kSteps + nl;
-    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    const int J0 = blockIdx.x * l.NPS * l.steps + nl;
+    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
     for (int J = J0; J < J1; J += l.NPS) {
         const int X = J % Wc, Y = (J / Wc) % C.H, t = J / WcHc;
         Quad q;
@@ -265,8 +269,8 @@ __global__ void __launch_bounds__(256) k_mg_up(Lvl F, Lvl C, int k, Lay l, const
     const int col = colok ? cg * 4 : 0;
     const int Wc = C.W, WcHc = C.W * C.H;
     float run[4] = {0.f, 0.f, 0.f, 0.f};
-    const int J0 = blockIdx.x * l.NPS * kSteps + nl;
-    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    const int J0 = blockIdx.x * l.NPS * l.steps + nl;
+    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
     if (colok) {
         for (int J = J0; J < J1; J += l.NPS) {
             const int X = J % Wc, Y = (J / Wc) % C.H, t = J / WcHc;
@@ -314,33 +318,28 @@ __global__ void __launch_bounds__(256) k_mg_up(Lvl F, Lvl C, int k, Lay l, const
     }
 }
 
-// coarsest level: kCoarseSweeps damped-Jacobi sweeps from zero, all nodes of the level in
-// one CTA per group of 4 columns (z ping-pongs in shared memory)
-__global__ void __launch_bounds__(256) k_mg_coarse(Lvl C, int k, const float *__restrict__ r, float *__restrict__ z) {
-    extern __shared__ __align__(16) float4 zsm[];  // [2][n]
-    const int col = blockIdx.x * 4;
-    const int n = (int)C.n;
-    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) zsm[i] = zero4();
-    __syncthreads();
-    for (int s = 0; s < kCoarseSweeps; ++s) {
-        const float4 *zin = zsm + (s & 1) * n;
-        float4 *zout = zsm + ((s + 1) & 1) * n;
-        auto val = [&](int j) { return zin[j]; };
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const float4 c = C.coef[i];
-            if (c.x == 0.f) {
-                zout[i] = zero4();
-                continue;
-            }
-            const float4 ri = f4ld(r + (int64_t)i * k + col);
-            const float4 zi = zin[i];
-            zout[i] = fma4(kOmega * fabsf(c.x),
-                           ri - apply_g<false>(C, i, i % C.W, (i / C.W) % C.H, c, zi, val, nullptr), zi);
+// coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
+// zero rows and columns at floating nodes) computed once on the host; one thread per node and
+// 4 columns, the inverse's row i read once per thread, r's rows shared through L1/L2
+__global__ void __launch_bounds__(256) k_mg_cinv(int n, int k, Lay l, const float *__restrict__ ainv,
+                                                 const float *__restrict__ r, float *__restrict__ z) {
+    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
+    const int cg = blockIdx.y * l.TPN + cgl;
+    if (cg >= l.KG) return;
+    const int col = cg * 4;
+    const int i0 = blockIdx.x * l.NPS * l.steps + nl;
+    const int i1 = min(n, (blockIdx.x + 1) * l.NPS * l.steps);
+    for (int i = i0; i < i1; i += l.NPS) {
+        const float *row = ainv + (int64_t)i * n;
+        float4 a0 = zero4(), a1 = zero4();
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+            a0 = fma4(row[j], f4ld(r + (int64_t)j * k + col), a0);
+            a1 = fma4(row[j + 1], f4ld(r + (int64_t)(j + 1) * k + col), a1);
         }
-        __syncthreads();
+        if (j < n) a0 = fma4(row[j], f4ld(r + (int64_t)j * k + col), a0);
+        f4st(z + (int64_t)i * k + col, a0 + a1);
     }
-    const float4 *zf = zsm + (kCoarseSweeps & 1) * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) f4st(z + (int64_t)i * k + col, zf[i]);
 }
 
 // ---- CG kernels (fine level) ----------------------------------------------------------
@@ -362,8 +361,8 @@ __global__ void __launch_bounds__(256) k_mg_spmv(Lvl F, int k, Lay l, const floa
     };
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float run[4] = {0.f, 0.f, 0.f, 0.f};
-    const int i0 = blockIdx.x * l.NPS * kSteps + nl;
-    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    const int i0 = blockIdx.x * l.NPS * l.steps + nl;
+    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
     if (colok) {
         for (int i = i0; i < i1; i += l.NPS) {
             const float4 c = F.coef[i];
@@ -396,8 +395,8 @@ __global__ void __launch_bounds__(256) k_mg_update(Lvl F, int k, Lay l, const do
                             : zero4();
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float run[4] = {0.f, 0.f, 0.f, 0.f};
-    const int i0 = blockIdx.x * l.NPS * kSteps + nl;
-    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * kSteps);
+    const int i0 = blockIdx.x * l.NPS * l.steps + nl;
+    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
     if (colok) {
         for (int i = i0; i < i1; i += l.NPS) {
             const int64_t o = (int64_t)i * k + col;
@@ -493,6 +492,7 @@ struct MgHier {
     std::vector<Lvl> lv;
     std::vector<float *> r, z;     // per level [n][k]; r[0] is the CG residual (not owned)
     float *q = nullptr;
+    float *ainv = nullptr;         // dense inverse of the coarsest level [n_c][n_c]
     double *part = nullptr;
     int64_t part_chunks = 0;
     int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
@@ -514,6 +514,7 @@ void free_mg(GridDev *g) {
     for (size_t i = 1; i < h->r.size(); ++i) cudaFree(h->r[i]);
     for (size_t i = 0; i < h->z.size(); ++i) cudaFree(h->z[i]);
     if (h->q) cudaFree(h->q);
+    if (h->ainv) cudaFree(h->ainv);
     if (h->part) cudaFree(h->part);
     if (h->cnt) cudaFree(h->cnt);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
@@ -521,28 +522,108 @@ void free_mg(GridDev *g) {
     g->mg = nullptr;
 }
 
+// A level's network, copied back from its device arrays (raw FP64 conductances).
+struct HostNet {
+    std::vector<double> gxr, gyr, tg, pg;
+    std::vector<int32_t> tptr, tnbr, pptr;
+    std::vector<uint8_t> fl;
+};
+
+static er_status fetch_net(const GridDev &f, HostNet &h) {
+    const int64_t n = f.n;
+    h.gxr.resize(n);
+    h.gyr.resize(n);
+    h.tptr.resize(n + 1);
+    h.pptr.resize(n + 1);
+    h.fl.resize(n);
+    ER_CUDA(cudaMemcpy(h.gxr.data(), f.gxr, n * sizeof(double), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(h.gyr.data(), f.gyr, n * sizeof(double), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(h.tptr.data(), f.tsv_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(h.pptr.data(), f.pad_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    ER_CUDA(cudaMemcpy(h.fl.data(), f.floating, n, cudaMemcpyDeviceToHost));
+    h.tnbr.resize(h.tptr[n]);
+    h.tg.resize(h.tptr[n]);
+    h.pg.resize(h.pptr[n]);
+    if (h.tptr[n]) {
+        ER_CUDA(cudaMemcpy(h.tnbr.data(), f.tsv_nbr, h.tptr[n] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        ER_CUDA(cudaMemcpy(h.tg.data(), f.tsv_g, h.tptr[n] * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (h.pptr[n]) ER_CUDA(cudaMemcpy(h.pg.data(), f.pad_g, h.pptr[n] * sizeof(double), cudaMemcpyDeviceToHost));
+    return ER_OK;
+}
+
+// Dense inverse of a (small) level's G in FP64 by Cholesky, G = L L^T, G^-1 = L^-T L^-1,
+// rounded to FP32; rows and columns of floating nodes are zero.
+static er_status dense_inverse(const GridDev &c, std::vector<float> &out) {
+    HostNet h;
+    er_status st = fetch_net(c, h);
+    if (st != ER_OK) return st;
+    const int n = (int)c.n, W = c.W;
+    std::vector<double> G((size_t)n * n, 0.0);
+    auto add_edge = [&](int a, int b, double g) {
+        G[(size_t)a * n + a] += g;
+        G[(size_t)b * n + b] += g;
+        G[(size_t)a * n + b] -= g;
+        G[(size_t)b * n + a] -= g;
+    };
+    for (int i = 0; i < n; ++i) {
+        if (h.fl[i]) {
+            G[(size_t)i * n + i] = 1.0;  // decoupled identity row; zeroed in the inverse
+            continue;
+        }
+        if (h.gxr[i] > 0.0) add_edge(i, i + 1, h.gxr[i]);
+        if (h.gyr[i] > 0.0) add_edge(i, i + W, h.gyr[i]);
+        for (int32_t e = h.tptr[i]; e < h.tptr[i + 1]; ++e)
+            if (h.tnbr[e] > i) add_edge(i, h.tnbr[e], h.tg[e]);
+        for (int32_t e = h.pptr[i]; e < h.pptr[i + 1]; ++e) G[(size_t)i * n + i] += h.pg[e];
+    }
+    // Cholesky, lower triangle in place (row-major)
+    for (int j = 0; j < n; ++j) {
+        double d = G[(size_t)j * n + j];
+        for (int q = 0; q < j; ++q) d -= G[(size_t)j * n + q] * G[(size_t)j * n + q];
+        if (!(d > 0.0)) return fail(ER_ERR_INVALID_ARG, "multigrid: coarsest level is not positive definite");
+        const double ljj = std::sqrt(d);
+        G[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = G[(size_t)i * n + j];
+            const double *li = &G[(size_t)i * n], *lj = &G[(size_t)j * n];
+            for (int q = 0; q < j; ++q) v -= li[q] * lj[q];
+            G[(size_t)i * n + j] = v / ljj;
+        }
+    }
+    // M = L^-1 (lower), then G^-1 = M^T M
+    std::vector<double> M((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        M[(size_t)i * n + i] = 1.0 / G[(size_t)i * n + i];
+        for (int j = 0; j < i; ++j) {
+            double v = 0.0;
+            for (int q = j; q < i; ++q) v += G[(size_t)i * n + q] * M[(size_t)q * n + j];
+            M[(size_t)i * n + j] = -v / G[(size_t)i * n + i];
+        }
+    }
+    out.assign((size_t)n * n, 0.0f);
+    for (int a = 0; a < n; ++a)
+        for (int b = a; b < n; ++b) {
+            double v = 0.0;
+            for (int q = b; q < n; ++q) v += M[(size_t)q * n + a] * M[(size_t)q * n + b];
+            const float f = (h.fl[a] || h.fl[b]) ? 0.0f : (float)v;
+            out[(size_t)a * n + b] = f;
+            out[(size_t)b * n + a] = f;
+        }
+    return ER_OK;
+}
+
 // The network of level l+1 from the device arrays of level l: aggregate 2 x 2 nodes per tier.
 static er_status coarsen(const GridDev &f, cudaStream_t s, er_grid **out) {
     const int T = f.T, W = f.W, H = f.H;
     const int Wc = (W + 1) / 2, Hc = (H + 1) / 2;
     const int64_t n = f.n;
-    std::vector<double> gxr(n), gyr(n), tg;
-    std::vector<int32_t> tptr(n + 1), tnbr, pptr(n + 1);
-    std::vector<double> pg;
-    std::vector<uint8_t> fl(n);
-    ER_CUDA(cudaMemcpy(gxr.data(), f.gxr, n * sizeof(double), cudaMemcpyDeviceToHost));
-    ER_CUDA(cudaMemcpy(gyr.data(), f.gyr, n * sizeof(double), cudaMemcpyDeviceToHost));
-    ER_CUDA(cudaMemcpy(tptr.data(), f.tsv_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    ER_CUDA(cudaMemcpy(pptr.data(), f.pad_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    ER_CUDA(cudaMemcpy(fl.data(), f.floating, n, cudaMemcpyDeviceToHost));
-    tnbr.resize(tptr[n]);
-    tg.resize(tptr[n]);
-    pg.resize(pptr[n]);
-    if (tptr[n]) {
-        ER_CUDA(cudaMemcpy(tnbr.data(), f.tsv_nbr, tptr[n] * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        ER_CUDA(cudaMemcpy(tg.data(), f.tsv_g, tptr[n] * sizeof(double), cudaMemcpyDeviceToHost));
-    }
-    if (pptr[n]) ER_CUDA(cudaMemcpy(pg.data(), f.pad_g, pptr[n] * sizeof(double), cudaMemcpyDeviceToHost));
+    HostNet hn;
+    er_status fst = fetch_net(f, hn);
+    if (fst != ER_OK) return fst;
+    const std::vector<double> &gxr = hn.gxr, &gyr = hn.gyr, &tg = hn.tg, &pg = hn.pg;
+    const std::vector<int32_t> &tptr = hn.tptr, &tnbr = hn.tnbr, &pptr = hn.pptr;
+    const std::vector<uint8_t> &fl = hn.fl;
     (void)s;
     auto id = [&](int t, int y, int x) { return ((int64_t)t * H + y) * W + x; };
     std::vector<double> gx((size_t)T * Hc * std::max(Wc - 1, 0), 0.0), gy((size_t)T * std::max(Hc - 1, 0) * Wc, 0.0);
@@ -588,7 +669,7 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
         h->grids.push_back(nullptr);
         h->lv.push_back(level_of(g));
         const GridDev *cur = &g;
-        while (std::max(cur->W, cur->H) > 8 || cur->n > kCoarseMax) {
+        while (cur->n > kCoarseTarget) {
             if (cur->W <= 1 && cur->H <= 1) break;
             er_grid *c = nullptr;
             er_status st = coarsen(*cur, s, &c);
@@ -600,10 +681,18 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
             h->lv.push_back(level_of(c->d));
             cur = &c->d;
         }
-        if (h->lv.back().n > kCoarseMax) {
+        if (h->lv.size() < 2 || h->lv.back().n > kCoarseMax) {
             free_mg(&g);
-            return fail(ER_ERR_INVALID_ARG, "multigrid: coarsest level too large (too many tiers)");
+            return fail(ER_ERR_INVALID_ARG, "multigrid: the grid does not coarsen to 2,048 nodes (too many tiers)");
         }
+        std::vector<float> inv;
+        er_status ist = dense_inverse(*cur, inv);
+        if (ist != ER_OK) {
+            free_mg(&g);
+            return ist;
+        }
+        ER_CUDA(cudaMalloc(&h->ainv, inv.size() * sizeof(float)));
+        ER_CUDA(cudaMemcpy(h->ainv, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice));
         ER_CUDA(cudaMalloc(&h->cnt, 2 * sizeof(int)));
         ER_CUDA(cudaMallocHost(&h->h_cnt, 2 * sizeof(int)));
     }
@@ -623,7 +712,7 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
             ER_CUDA(cudaMalloc(&h->z[l], bytes));
         }
         ER_CUDA(cudaMalloc(&h->q, (size_t)g.n * k * sizeof(float)));
-        h->part_chunks = make_lay(g.n, k).chunks;
+        h->part_chunks = std::max(make_lay(g.n, k).chunks, make_lay(h->lv[1].n, k).chunks);
         ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(double)));
         h->k = k;
     }
@@ -678,8 +767,9 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
                   h.lv[l], h.lv[l + 1], k, lc, rl, h.r[l + 1]);
     }
     const Lvl &C = h.lv[L - 1];
-    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_coarse, dim3((unsigned)(k / 4)), (int)(2 * C.n * sizeof(float4)), C, k,
-              (const float *)h.r[L - 1], h.z[L - 1]);
+    const Lay lco = make_lay(C.n, k);
+    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, dim3((unsigned)lco.chunks, lco.ncb), 0, (int)C.n, k, lco,
+              (const float *)h.ainv, (const float *)h.r[L - 1], h.z[L - 1]);
     for (int l = L - 2; l >= 0; --l) {
         const Lay lc = make_lay(h.lv[l + 1].n, k);  // one thread per aggregate of level l + 1
         const float *rl = l == 0 ? r0 : h.r[l];
@@ -722,16 +812,6 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     MgHier *h = nullptr;
     er_status st = get_mg(g, k, w.s, &h);
     if (st != ER_OK) return st;
-    const Lvl &C = h->lv.back();
-    {
-        static bool attr = false;
-        if (!attr) {
-            ER_CUDA(cudaFuncSetAttribute(k_mg_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * kCoarseMax * sizeof(float4))));
-            attr = true;
-        }
-    }
-    (void)C;
     MgRun m{&g, &w, h, k, tol, Z};
     Prof pf;
     pf.on = opt.profile != 0;

@@ -459,8 +459,9 @@ er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision pr
     ER_CUDA(cudaStreamWaitEvent(w.s, w.ev, 0));
     std::vector<double> resid((size_t)k);
     w.h_resid = resid.data();
-    // a grid too small to coarsen (at most 8 x 8 per tier) has a one-level hierarchy: Jacobi
-    const bool mg = opt.precond == 1 && (std::max(g.W, g.H) > 8 || g.n > 2048);
+    // a grid of at most 512 nodes is the multigrid's coarsest level itself, and 1 x 1 tiers do
+    // not coarsen: both use Jacobi
+    const bool mg = opt.precond == 1 && g.n > 512 && std::max(g.W, g.H) > 1;
     st = mg ? mg_solve_core(g, w, Yt, Z, opt, stats, t0) : solve_core(g, w, Yt, Z, prec, opt, stats, t0);
     w.h_resid = nullptr;
     return st;
