@@ -22,10 +22,11 @@
 // with the FP64 residual substituted every replace_every iterations, and whenever every
 // column's recursive residual meets tol; a column stops only when that FP64 residual meets
 // tol, and a column whose recursion ran past its attainable accuracy restarts its search
-// direction), in four kernels per iteration: the V-cycle
-// (whose last kernel also forms r.z), p' = z + beta p with q = G p' and the energy p'.G p',
-// the update x += alpha p', r -= alpha q with r.D^-1 r, and small per-column folds that
-// sum per-CTA partials in a fixed order (results are identical from run to run).
+// direction), in three stages per iteration: the V-cycle (whose last kernel also forms r.z),
+// p' = z + beta p with the energy p'.G p', and r -= alpha G p' with G p' recomputed from p'
+// (never stored) and r.D^-1 r; x takes two iterations' steps every second iteration; small
+// per-column folds sum per-CTA partials in a fixed order (results are identical from run to
+// run).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256) k_mg_down(Lvl F, Lvl C, int k, Lay l, con
 // and 4 columns: v = z0 + s P zc on the four children, then z = v + w D^-1 (r - G v); with
 // DOT the CTA also writes its partials of r.z
 template <bool DOT>
-__global__ void __launch_bounds__(256) k_mg_up(Lvl F, Lvl C, int k, Lay l, const float *__restrict__ r,
+__global__ void __launch_bounds__(256, 3) k_mg_up(Lvl F, Lvl C, int k, Lay l, const float *__restrict__ r,
                                                const float *__restrict__ zc, float *__restrict__ z, double *part) {
     const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
     const int cg = blockIdx.y * l.TPN + cgl;
@@ -344,10 +345,11 @@ __global__ void __launch_bounds__(256) k_mg_cinv(int n, int k, Lay l, const floa
 
 // ---- CG kernels (fine level) ----------------------------------------------------------
 
-// p' = z + beta p; q = G p'; partials of p'.G p' (edge energy)
+// p' = z + beta p; partials of p'.G p' (edge energy).  q = G p' is not stored: the update
+// pass recomputes it from p' (a stencil on FP32 costs less than a vector round trip).
 __global__ void __launch_bounds__(256) k_mg_spmv(Lvl F, int k, Lay l, const float *__restrict__ z,
                                                  const float *__restrict__ p, const double *__restrict__ beta,
-                                                 float *__restrict__ p_out, float *__restrict__ q, double *part) {
+                                                 float *__restrict__ p_out, double *part) {
     const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
     const int cg = blockIdx.y * l.TPN + cgl;
     const bool colok = cg < l.KG;
@@ -366,15 +368,14 @@ __global__ void __launch_bounds__(256) k_mg_spmv(Lvl F, int k, Lay l, const floa
     if (colok) {
         for (int i = i0; i < i1; i += l.NPS) {
             const float4 c = F.coef[i];
-            float4 pv = zero4(), qv = zero4();
+            float4 pv = zero4();
             if (c.x != 0.f) {
                 pv = val(i);
                 float4 en;
-                qv = apply_g<true>(F, i, i % F.W, (i / F.W) % F.H, c, pv, val, &en);
+                (void)apply_g<true>(F, i, i % F.W, (i / F.W) % F.H, c, pv, val, &en);
                 run[0] += en.x; run[1] += en.y; run[2] += en.z; run[3] += en.w;
             }
             f4st(p_out + (int64_t)i * k + col, pv);
-            f4st(q + (int64_t)i * k + col, qv);
         }
     }
 #pragma unroll
@@ -382,17 +383,23 @@ __global__ void __launch_bounds__(256) k_mg_spmv(Lvl F, int k, Lay l, const floa
     block_partials(l, k, cg, colok, acc, part);
 }
 
-// x += alpha p'; r -= alpha q; partials of r.D^-1 r
+// r -= alpha G p' (G p' recomputed from p'); partials of r.D^-1 r.  With XPAIR (every second
+// iteration) also x += alpha_prev p'_prev + alpha p': x takes two iterations' steps at once.
+template <bool XPAIR>
 __global__ void __launch_bounds__(256) k_mg_update(Lvl F, int k, Lay l, const double *__restrict__ alpha,
-                                                   const float *__restrict__ p, const float *__restrict__ q,
-                                                   float *__restrict__ x, float *__restrict__ r, double *part) {
+                                                   const double *__restrict__ alpha_prev, const float *__restrict__ p,
+                                                   const float *__restrict__ p_prev, float *__restrict__ x,
+                                                   float *__restrict__ r, double *part) {
     const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
     const int cg = blockIdx.y * l.TPN + cgl;
     const bool colok = cg < l.KG;
     const int col = colok ? cg * 4 : 0;
-    const float4 a4 = colok ? make_float4((float)alpha[col], (float)alpha[col + 1], (float)alpha[col + 2],
-                                          (float)alpha[col + 3])
-                            : zero4();
+    auto ld4d = [&](const double *a) {
+        return colok ? make_float4((float)a[col], (float)a[col + 1], (float)a[col + 2], (float)a[col + 3]) : zero4();
+    };
+    const float4 a4 = ld4d(alpha);
+    const float4 ap4 = XPAIR ? ld4d(alpha_prev) : zero4();
+    auto val = [&](int j) { return f4ld(p + (int64_t)j * k + col); };
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float run[4] = {0.f, 0.f, 0.f, 0.f};
     const int i0 = blockIdx.x * l.NPS * l.steps + nl;
@@ -400,12 +407,14 @@ __global__ void __launch_bounds__(256) k_mg_update(Lvl F, int k, Lay l, const do
     if (colok) {
         for (int i = i0; i < i1; i += l.NPS) {
             const int64_t o = (int64_t)i * k + col;
-            const float4 pv = f4ld(p + o), qv = f4ld(q + o);
-            const float4 xv = f4ld(x + o) + a4 * pv;
+            const float4 c = F.coef[i];
+            if (c.x == 0.f) continue;  // floating: r, x and p' stay 0
+            const float4 pv = f4ld(p + o);
+            const float4 qv = apply_g<false>(F, i, i % F.W, (i / F.W) % F.H, c, pv, val, nullptr);
             const float4 rv = f4ld(r + o) - a4 * qv;
-            f4st(x + o, xv);
             f4st(r + o, rv);
-            const float di = fabsf(F.coef[i].x);
+            if constexpr (XPAIR) f4st(x + o, f4ld(x + o) + ap4 * f4ld(p_prev + o) + a4 * pv);
+            const float di = fabsf(c.x);
             run[0] = fmaf(di * rv.x, rv.x, run[0]);
             run[1] = fmaf(di * rv.y, rv.y, run[1]);
             run[2] = fmaf(di * rv.z, rv.z, run[2]);
@@ -427,6 +436,7 @@ struct FoldArgs {
     int k;
     double *alpha, *beta, *rho, *rho0;
     double *relrec;  // recursive residual ||r||_{D^-1} / ||b||_{D^-1} per column (FOLD_RR)
+    double *alpha_prev;  // FOLD_ALPHA keeps the previous alpha (x is updated in pairs)
     int *active;
     int *nunc;  // columns still above tol (FOLD_RR adds, FOLD_BETA resets)
     double tol;
@@ -448,6 +458,7 @@ __global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
     const double tot = s[0];
     const bool act = f.active[j] != 0;
     if constexpr (KIND == FOLD_ALPHA) {
+        f.alpha_prev[j] = f.alpha[j];
         f.alpha[j] = (act && tot > 0.0 && isfinite(tot)) ? f.rho[j] / tot : 0.0;
     } else if constexpr (KIND == FOLD_RR) {
         const double rel = f.rho0[j] > 0.0 ? sqrt(tot / f.rho0[j]) : 0.0;
@@ -491,8 +502,8 @@ struct MgHier {
     std::vector<er_grid *> grids;  // level l >= 1; grids[0] = nullptr (the fine grid)
     std::vector<Lvl> lv;
     std::vector<float *> r, z;     // per level [n][k]; r[0] is the CG residual (not owned)
-    float *q = nullptr;
     float *ainv = nullptr;         // dense inverse of the coarsest level [n_c][n_c]
+    double *msc = nullptr;         // per column: recursive residual, previous alpha [2][k]
     double *part = nullptr;
     int64_t part_chunks = 0;
     int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
@@ -513,8 +524,8 @@ void free_mg(GridDev *g) {
     for (size_t i = 1; i < h->grids.size(); ++i) er_grid_destroy(h->grids[i]);
     for (size_t i = 1; i < h->r.size(); ++i) cudaFree(h->r[i]);
     for (size_t i = 0; i < h->z.size(); ++i) cudaFree(h->z[i]);
-    if (h->q) cudaFree(h->q);
     if (h->ainv) cudaFree(h->ainv);
+    if (h->msc) cudaFree(h->msc);
     if (h->part) cudaFree(h->part);
     if (h->cnt) cudaFree(h->cnt);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
@@ -699,11 +710,9 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
     if (h->k != k) {
         for (size_t i = 1; i < h->r.size(); ++i) cudaFree(h->r[i]);
         for (size_t i = 0; i < h->z.size(); ++i) cudaFree(h->z[i]);
-        if (h->q) cudaFree(h->q);
         if (h->part) cudaFree(h->part);
         h->r.assign(h->lv.size(), nullptr);
         h->z.assign(h->lv.size(), nullptr);
-        h->q = nullptr;
         h->part = nullptr;
         h->k = 0;
         for (size_t l = 0; l < h->lv.size(); ++l) {
@@ -711,8 +720,9 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
             if (l > 0) ER_CUDA(cudaMalloc(&h->r[l], bytes));
             ER_CUDA(cudaMalloc(&h->z[l], bytes));
         }
-        ER_CUDA(cudaMalloc(&h->q, (size_t)g.n * k * sizeof(float)));
         h->part_chunks = std::max(make_lay(g.n, k).chunks, make_lay(h->lv[1].n, k).chunks);
+        if (h->msc) cudaFree(h->msc);
+        ER_CUDA(cudaMalloc(&h->msc, (size_t)2 * k * sizeof(double)));
         ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(double)));
         h->k = k;
     }
@@ -749,7 +759,8 @@ FoldArgs fold_args(const MgRun &m, int64_t chunks) {
     f.beta = m.w->scal + m.k;
     f.rho = m.w->scal + 2 * m.k;
     f.rho0 = m.w->scal + 3 * m.k;
-    f.relrec = m.w->scal + 5 * m.k;
+    f.relrec = m.h->msc;
+    f.alpha_prev = m.h->msc + m.k;
     f.active = m.w->ints;
     f.nunc = m.h->cnt;
     f.tol = m.tol;
@@ -784,8 +795,9 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
               fold_args(m, make_lay(h.lv[1].n, k).chunks));
 }
 
-// one PCG iteration from the current residual w.r[0]: z = M r, beta, p' = z + beta p,
-// q = G p', alpha, x += alpha p', r -= alpha q, recursive residual norms
+// one PCG iteration from the current residual w.r[0]: z = M r, beta, p' = z + beta p and
+// p'.G p', alpha, r -= alpha G p' with the recursive residual norms, and every second
+// iteration x += alpha_prev p'_prev + alpha p'
 int mg_iterate(const MgRun &m, int cur, Prof *pf) {
     MgHier &h = *m.h;
     Workspace &w = *m.w;
@@ -795,10 +807,16 @@ int mg_iterate(const MgRun &m, int cur, Prof *pf) {
     const Lay lf = make_lay(m.g->n, k);
     const dim3 grid((unsigned)lf.chunks, lf.ncb);
     mg_launch(w, pf, ER_PASS_A, k_mg_spmv, grid, 0, h.lv[0], k, lf, (const float *)h.z[0], (const float *)w.p[cur],
-              (const double *)(w.scal + k), (float *)w.p[1 - cur], h.q, h.part);
+              (const double *)(w.scal + k), (float *)w.p[1 - cur], h.part);
     mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_ALPHA>, dim3((unsigned)k), 0, fold_args(m, lf.chunks));
-    mg_launch(w, pf, ER_PASS_B, k_mg_update, grid, 0, h.lv[0], k, lf, (const double *)w.scal,
-              (const float *)w.p[1 - cur], (const float *)h.q, (float *)m.Z, r, h.part);
+    if (cur == 1)  // second iteration of a pair: x += alpha_prev p'_prev + alpha p'
+        mg_launch(w, pf, ER_PASS_B, k_mg_update<true>, grid, 0, h.lv[0], k, lf, (const double *)w.scal,
+                  (const double *)(h.msc + k), (const float *)w.p[1 - cur], (const float *)w.p[cur], (float *)m.Z, r,
+                  h.part);
+    else
+        mg_launch(w, pf, ER_PASS_B0, k_mg_update<false>, grid, 0, h.lv[0], k, lf, (const double *)w.scal,
+                  (const double *)(h.msc + k), (const float *)w.p[1 - cur], (const float *)w.p[cur], (float *)m.Z, r,
+                  h.part);
     mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_RR>, dim3((unsigned)k), 0, fold_args(m, lf.chunks));
     return 1 - cur;
 }
@@ -836,7 +854,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
         fp32_residual(g, w, Yt, tol, 0, 0, &pf);
         ER_CUDA(cudaMemsetAsync(h->cnt + 1, 0, sizeof(int), w.s));
         prof_begin(w, &pf, ER_PASS_OTHER);
-        k_mg_freeze<<<ublocks(k, 128), 128, 0, w.s>>>(k, w.scal + 4 * k, w.scal + 5 * k, tol, w.ints,
+        k_mg_freeze<<<ublocks(k, 128), 128, 0, w.s>>>(k, w.scal + 4 * k, h->msc, tol, w.ints,
                                                        w.scal + 2 * k, h->cnt + 1);
         prof_end(w, &pf, ER_PASS_OTHER);
         ER_CUDA(cudaGetLastError());
@@ -853,7 +871,8 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     cudaGraphExec_t gexec = nullptr;
     int g_parity = -1;
     while (!done && it < opt.maxit) {
-        const int todo = std::min(block, opt.maxit - it);
+        int todo = std::min(block, opt.maxit - it);
+        if (todo & 1) ++todo;  // x is updated in iteration pairs
         if (use_graph && todo == block) {
             if (!gexec || g_parity != cur) {
                 if (gexec) cudaGraphExecDestroy(gexec);
@@ -871,7 +890,8 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
             ER_CUDA(cudaGraphLaunch(gexec, w.s));
             const int L = (int)h->lv.size();
             pf.launches[ER_PASS_A] += block;
-            pf.launches[ER_PASS_B] += block;
+            pf.launches[ER_PASS_B] += block / 2;
+            pf.launches[ER_PASS_B0] += block / 2;
             pf.launches[ER_PASS_MG] += block * (2 * L - 3);
             pf.launches[ER_PASS_MG_DOWN] += block;
             pf.launches[ER_PASS_MG_UP] += block;
