@@ -966,7 +966,8 @@ def main():
                        "nodes_per_rank": int(n_total / world),
                        "preconditioner": "aggregation multigrid V-cycle" if (args.precond == "mg" and args.prec == "fp32")
                        else "Jacobi",
-                       "l2": "inputs larger than L2 (each [n][k] array is 1 GiB)",
+                       "l2": f"inputs larger than L2 (each [n][k] array is "
+                             f"{int(n_total / world) * args.k * (4 if args.prec == 'fp32' else 8) / 2**30:.2f} GiB)",
                        "iterations_per_step": result["rank0_iterations"],
                        "fp64_residual_replacements_per_step": result["replacements"],
                        "tol": args.tol if args.tol is not None else ("1e-7" if args.prec == "fp32" else "1e-12"),
