@@ -33,6 +33,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "er_common.cuh"
 
 namespace er {
@@ -319,6 +321,211 @@ __global__ void __launch_bounds__(256, 3) k_mg_up(Lvl F, Lvl C, int k, Lay l, co
     }
 }
 
+// ---- TMA-tiled restriction and prolongation ------------------------------------------------
+//
+// A CTA owns a tile of 16 x 4 aggregates of one tier (32 x 8 nodes of the finer level) and 32
+// RHS columns.  One thread issues three cp.async.bulk.tensor loads into shared memory: the
+// finer level's r and coefficients over the tile plus a one-node halo (34 x 10 nodes; the box's
+// zero fill is the mesh edge) and, for the prolongation, the coarse correction over the tile's
+// aggregates plus a one-aggregate halo (18 x 6).  The threads then work from shared memory:
+// thread item = (aggregate, group of 4 columns), 8 column groups of 4 aggregates per warp, so
+// every quarter-warp reads 128 contiguous bytes.  Only TSV partners (other tiers) are read from
+// global memory.  The wait on the loads is bounded: on expiry the CTA raises the error word,
+// waits (bounded) for its own copies and returns.
+
+constexpr int TAX = 16, TAY = 4;                 // aggregates per tile
+constexpr int TFX = 2 * TAX + 2, TFY = 2 * TAY + 2;  // finer-level nodes per tile, with halo
+constexpr int TZX = TAX + 2, TZY = TAY + 2;      // aggregates per tile, with halo
+constexpr int TCB = 32;                          // RHS columns per CTA
+constexpr int T_R = TFY * TFX * TCB * 4;         // 43,520 bytes
+constexpr int T_C = ((TFY * TFX * 16 + 127) / 128) * 128;
+constexpr int T_Z = TZY * TZX * TCB * 4;         // 13,824 bytes
+constexpr int T_SMEM = T_R + T_C + T_Z + 128;
+constexpr uint32_t kTileSpin = 1u << 22;
+
+int64_t n_tiles(const Lvl &C) {
+    return (int64_t)((C.W + TAX - 1) / TAX) * ((C.H + TAY - 1) / TAY) * C.T;
+}
+
+dim3 tile_grid(const Lvl &C, int k) { return dim3((unsigned)n_tiles(C), (unsigned)((k + TCB - 1) / TCB)); }
+
+__device__ __forceinline__ uint32_t mg_saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mg_tma4(void *dst, const CUtensorMap *m, uint64_t *bar, int c0, int c1, int c2,
+                                        int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(mg_saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mg_saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mg_try_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mg_saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Issue the tile's loads and wait for them.  Returns false (error word raised) on expiry.
+__device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, const CUtensorMap *mr,
+                                          const CUtensorMap *mc, const CUtensorMap *mz, int c0, int X0, int Y0, int t,
+                                          int *err) {
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint32_t bytes = (uint32_t)(T_R + TFY * TFX * 16 + (mz ? T_Z : 0));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mg_saddr(bar)), "r"(bytes)
+                     : "memory");
+        mg_tma4(sm, mr, bar, c0, 2 * X0 - 1, 2 * Y0 - 1, t);
+        mg_tma4(sm + T_R, mc, bar, 0, 2 * X0 - 1, 2 * Y0 - 1, t);
+        if (mz) mg_tma4(sm + T_R + T_C, mz, bar, c0, X0 - 1, Y0 - 1, t);
+    }
+    __syncthreads();
+    // every thread waits (bounded); the vote makes the outcome uniform across the CTA
+    bool done = true;
+    for (uint32_t spins = 0; !mg_try_wait(bar, 0);) {
+        if (++spins > kTileSpin) {
+            done = false;
+            break;
+        }
+    }
+    if (__syncthreads_and(done ? 1 : 0)) return true;
+    if (threadIdx.x == 0) {  // raise the error word and let this CTA's own copies land first
+        atomicExch(err, 1);
+        for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar, 0); ++q) {
+        }
+    }
+    return false;
+}
+
+struct TileGeo {
+    int X0, Y0, t, c0;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const Lvl &C) {
+    const int tx = (C.W + TAX - 1) / TAX, ty = (C.H + TAY - 1) / TAY;
+    TileGeo g;
+    int b = blockIdx.x;
+    g.X0 = (b % tx) * TAX;
+    b /= tx;
+    g.Y0 = (b % ty) * TAY;
+    g.t = b / ty;
+    g.c0 = blockIdx.y * TCB;
+    return g;
+}
+
+// prolongation + post-sweep (UP) or pre-sweep + restriction (!UP) over one tile
+template <bool UP, bool DOT>
+__global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtensorMap mr,
+                                                 const __grid_constant__ CUtensorMap mc,
+                                                 const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
+                                                 const float *__restrict__ r, const float *__restrict__ zc,
+                                                 float *__restrict__ out, double *part, int *err) {
+    extern __shared__ unsigned char mg_tile_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char *sm = mg_tile_raw + ((128u - (mg_saddr(mg_tile_raw) & 127u)) & 127u);
+    const float *rs = reinterpret_cast<const float *>(sm);
+    const float4 *cs = reinterpret_cast<const float4 *>(sm + T_R);
+    const float *zs = reinterpret_cast<const float *>(sm + T_R + T_C);
+    const TileGeo g = tile_geo(C);
+    const bool ok = tile_load(sm, &bar, &mr, &mc, UP ? &mz : nullptr, g.c0, g.X0, g.Y0, g.t, err);
+    if (!ok) return;
+    const int Wc = C.W, WcHc = C.W * C.H;
+    float run[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int item = threadIdx.x + 256 * h;
+        const int cg = item & 7, a = item >> 3;
+        const int ax = a % TAX, ay = a / TAX;
+        const int X = g.X0 + ax, Y = g.Y0 + ay;
+        const int col = g.c0 + cg * 4;
+        if (X >= C.W || Y >= C.H || col >= k) continue;
+        const int J = (g.t * C.H + Y) * Wc + X;
+        // value of the smoothed field at tile node (ly, lx)
+        auto sval = [&](int ly, int lx) {
+            const float4 c = cs[ly * TFX + lx];
+            const float4 rv = *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
+            float4 v = (kOmega * fabsf(c.x)) * rv;
+            if constexpr (UP)
+                v = fma4(kScale, *reinterpret_cast<const float4 *>(zs + (((ly + 1) >> 1) * TZX + ((lx + 1) >> 1)) * TCB +
+                                                                    cg * 4), v);
+            return v;
+        };
+        auto gval = [&](int j, int dJ) {  // TSV partner on another tier (global memory)
+            const float4 cj = F.coef[j];
+            float4 v = (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col);
+            if constexpr (UP) v = fma4(kScale, f4ld(zc + (int64_t)(J + dJ) * k + col), v);
+            return v;
+        };
+        float4 acc = zero4();
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int x = 2 * X + dx, y = 2 * Y + dy;
+                if (x >= F.W || y >= F.H) continue;
+                const int lx = 1 + 2 * ax + dx, ly = 1 + 2 * ay + dy;
+                const float4 c = cs[ly * TFX + lx];
+                const int i = (g.t * F.H + y) * F.W + x;
+                if (c.x == 0.f) {  // floating node: not in P, z = 0
+                    if constexpr (UP) f4st(out + (int64_t)i * k + col, zero4());
+                    continue;
+                }
+                const float4 ri = *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
+                const float4 vi = sval(ly, lx);
+                float4 gv = c.w * vi;
+                if (c.y != 0.f) gv = fma4(c.y, vi - sval(ly, lx + 1), gv);
+                {
+                    const float gw = cs[ly * TFX + lx - 1].y;
+                    if (gw != 0.f) gv = fma4(gw, vi - sval(ly, lx - 1), gv);
+                }
+                if (c.z != 0.f) gv = fma4(c.z, vi - sval(ly + 1, lx), gv);
+                {
+                    const float gn = cs[(ly - 1) * TFX + lx].z;
+                    if (gn != 0.f) gv = fma4(gn, vi - sval(ly - 1, lx), gv);
+                }
+                if (c.x < 0.f) {
+                    const int32_t e1 = F.tsv_ptr[i + 1];
+                    for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
+                        const int j = F.tsv_nbr[e];
+                        gv = fma4(F.tsv_g[e], vi - gval(j, j > i ? WcHc : -WcHc), gv);
+                    }
+                }
+                if constexpr (UP) {
+                    const float4 zo = fma4(kOmega * fabsf(c.x), ri - gv, vi);
+                    f4st(out + (int64_t)i * k + col, zo);
+                    if constexpr (DOT) {
+                        run[h][0] = fmaf(ri.x, zo.x, run[h][0]);
+                        run[h][1] = fmaf(ri.y, zo.y, run[h][1]);
+                        run[h][2] = fmaf(ri.z, zo.z, run[h][2]);
+                        run[h][3] = fmaf(ri.w, zo.w, run[h][3]);
+                    }
+                } else {
+                    acc = acc + (ri - gv);
+                }
+            }
+        if constexpr (!UP) f4st(out + (int64_t)J * k + col, acc);
+    }
+    if constexpr (DOT) {
+        // per column: the 64 items of the tile that share it, summed in a fixed order
+        __shared__ double sred[256 * 4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sred[threadIdx.x * 4 + v] = (double)run[0][v] + (double)run[1][v];
+        __syncthreads();
+        if (threadIdx.x < TCB) {
+            const int cg = threadIdx.x >> 2, v = threadIdx.x & 3;
+            double sacc = 0.0;
+            for (int q = cg; q < 256; q += 8) sacc += sred[q * 4 + v];
+            const int col = g.c0 + threadIdx.x;
+            if (col < k) part[(int64_t)blockIdx.x * k + col] = sacc;
+        }
+    }
+}
+
 // coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
 // zero rows and columns at floating nodes) computed once on the host; one thread per node and
 // 4 columns, the inverse's row i read once per thread, r's rows shared through L1/L2
@@ -495,6 +702,36 @@ unsigned ublocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
+// ---- tensor maps of the tiled kernels ------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 mg_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 4-D FP32 map over [T][H][W][d0] (d0 innermost) with a box of b0 x bx x by x 1
+static er_status mg_map(CUtensorMap *m, const void *base, int64_t d0, const Lvl &L, int b0, int bx, int by) {
+    auto fn = mg_encode();
+    if (!fn) return fail(ER_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[4] = {(cuuint64_t)d0, (cuuint64_t)L.W, (cuuint64_t)L.H, (cuuint64_t)L.T};
+    cuuint64_t strides[3] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * 4 * L.W, (cuuint64_t)d0 * 4 * L.W * L.H};
+    cuuint32_t box[4] = {(cuuint32_t)b0, (cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ER_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return ER_OK;
+}
+
 // ---- hierarchy ---------------------------------------------------------------------------
 
 struct MgHier {
@@ -504,6 +741,8 @@ struct MgHier {
     std::vector<float *> r, z;     // per level [n][k]; r[0] is the CG residual (not owned)
     float *ainv = nullptr;         // dense inverse of the coarsest level [n_c][n_c]
     double *msc = nullptr;         // per column: recursive residual, previous alpha [2][k]
+    // tiled kernels, per level l: r_l (finer side), coefficients, z_l (coarser side of l - 1)
+    std::vector<CUtensorMap> map_r, map_c, map_z;
     double *part = nullptr;
     int64_t part_chunks = 0;
     int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
@@ -720,7 +959,7 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
             if (l > 0) ER_CUDA(cudaMalloc(&h->r[l], bytes));
             ER_CUDA(cudaMalloc(&h->z[l], bytes));
         }
-        h->part_chunks = std::max(make_lay(g.n, k).chunks, make_lay(h->lv[1].n, k).chunks);
+        h->part_chunks = std::max(make_lay(g.n, k).chunks, n_tiles(h->lv[1]));
         if (h->msc) cudaFree(h->msc);
         ER_CUDA(cudaMalloc(&h->msc, (size_t)2 * k * sizeof(double)));
         ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(double)));
@@ -741,7 +980,9 @@ struct MgRun {
     int k;
     double tol;
     void *Z;
+    int *err;  // the solve's error word (a bounded wait expired)
 };
+
 
 template <class K, class... A>
 void mg_launch(Workspace &w, Prof *pf, int kind, K kern, dim3 grid, int smem, A... args) {
@@ -772,27 +1013,26 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     MgHier &h = *m.h;
     const int L = (int)h.lv.size(), k = m.k;
     for (int l = 0; l + 1 < L; ++l) {
-        const Lay lc = make_lay(h.lv[l + 1].n, k);
         const float *rl = l == 0 ? r0 : h.r[l];
-        mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_down, dim3((unsigned)lc.chunks, lc.ncb), 0,
-                  h.lv[l], h.lv[l + 1], k, lc, rl, h.r[l + 1]);
+        mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_tile<false, false>, tile_grid(h.lv[l + 1], k),
+                  T_SMEM, h.map_r[l], h.map_c[l], h.map_r[l], h.lv[l], h.lv[l + 1], k, rl, (const float *)nullptr,
+                  h.r[l + 1], (double *)nullptr, m.err);
     }
     const Lvl &C = h.lv[L - 1];
     const Lay lco = make_lay(C.n, k);
     mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, dim3((unsigned)lco.chunks, lco.ncb), 0, (int)C.n, k, lco,
               (const float *)h.ainv, (const float *)h.r[L - 1], h.z[L - 1]);
     for (int l = L - 2; l >= 0; --l) {
-        const Lay lc = make_lay(h.lv[l + 1].n, k);  // one thread per aggregate of level l + 1
         const float *rl = l == 0 ? r0 : h.r[l];
         if (l == 0)
-            mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_up<true>, dim3((unsigned)lc.chunks, lc.ncb), 0, h.lv[l],
-                      h.lv[l + 1], k, lc, rl, (const float *)h.z[l + 1], h.z[l], h.part);
+            mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_tile<true, true>, tile_grid(h.lv[1], k), T_SMEM, h.map_r[0],
+                      h.map_c[0], h.map_z[1], h.lv[0], h.lv[1], k, rl, (const float *)h.z[1], h.z[0], h.part, m.err);
         else
-            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_up<false>, dim3((unsigned)lc.chunks, lc.ncb), 0, h.lv[l],
-                      h.lv[l + 1], k, lc, rl, (const float *)h.z[l + 1], h.z[l], (double *)nullptr);
+            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<true, false>, tile_grid(h.lv[l + 1], k), T_SMEM, h.map_r[l],
+                      h.map_c[l], h.map_z[l + 1], h.lv[l], h.lv[l + 1], k, rl, (const float *)h.z[l + 1], h.z[l],
+                      (double *)nullptr, m.err);
     }
-    mg_launch(*m.w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_BETA>, dim3((unsigned)k), 0,
-              fold_args(m, make_lay(h.lv[1].n, k).chunks));
+    mg_launch(*m.w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_BETA>, dim3((unsigned)k), 0, fold_args(m, n_tiles(h.lv[1])));
 }
 
 // one PCG iteration from the current residual w.r[0]: z = M r, beta, p' = z + beta p and
@@ -830,7 +1070,27 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     MgHier *h = nullptr;
     er_status st = get_mg(g, k, w.s, &h);
     if (st != ER_OK) return st;
-    MgRun m{&g, &w, h, k, tol, Z};
+    {
+        const int L = (int)h->lv.size();
+        h->map_r.resize(L);
+        h->map_c.resize(L);
+        h->map_z.resize(L);
+        for (int l = 0; l < L; ++l) {
+            const void *rl = l == 0 ? w.r[0] : (const void *)h->r[l];
+            er_status ms = mg_map(&h->map_r[l], rl, k, h->lv[l], TCB, TFX, TFY);
+            if (ms == ER_OK) ms = mg_map(&h->map_c[l], h->lv[l].coef, 4, h->lv[l], 4, TFX, TFY);
+            if (ms == ER_OK) ms = mg_map(&h->map_z[l], h->z[l], k, h->lv[l], TCB, TZX, TZY);
+            if (ms != ER_OK) return ms;
+        }
+        static bool attr = false;
+        if (!attr) {
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+            attr = true;
+        }
+    }
+    MgRun m{&g, &w, h, k, tol, Z, w.ints + w.k + w.til.n_colblk};
     Prof pf;
     pf.on = opt.profile != 0;
     const bool use_graph = opt.use_graph && !pf.on;
