@@ -11,22 +11,25 @@
 //     er_grid_create from the aggregated network, and every level runs the same stencil;
 //   * V-cycle on level l with right-hand side r: z0 = w D^-1 r (one damped-Jacobi sweep
 //     from zero), r_c = P^T (r - G z0), z_c = V-cycle on level l+1, z = z0 + s P z_c, and
-//     one damped-Jacobi post-sweep z += w D^-1 (r - G z); the coarsest level (at most 8 x 8
-//     per tier) runs a fixed number of damped-Jacobi sweeps from zero.  Every step is a fixed
-//     linear map and the pre- and post-sweeps are each other's adjoints, so the V-cycle is a
-//     symmetric operator, as CG requires;
-//   * the pre-sweep and restriction are one kernel per level (a thread owns one aggregate and
-//     one group of 4 RHS columns); prolongation and post-sweep are one kernel per level; z0
-//     is never stored, it is recomputed from r.
+//     one damped-Jacobi post-sweep z += w D^-1 (r - G z); the coarsest level is solved
+//     exactly.  Every step is a fixed linear map and the pre- and post-sweeps are each
+//     other's adjoints, so the V-cycle is a symmetric positive definite operator, as CG
+//     requires;
+//   * the pre-sweep and restriction are one kernel per level, and prolongation and post-sweep
+//     another: a CTA owns 16 x 4 aggregates (32 x 8 nodes of the finer level) and 32 RHS
+//     columns, staged with a one-node halo by cp.async.bulk.tensor; z0 is never stored, it is
+//     recomputed from r; the coarsest level (at most 512 nodes) is solved exactly by its dense
+//     inverse.
 // The CG recursion is the FP32 form's (FP32 vectors, FP64-accumulated dots, FP64 iterate
 // with the FP64 residual substituted every replace_every iterations, and whenever every
 // column's recursive residual meets tol; a column stops only when that FP64 residual meets
 // tol, and a column whose recursion ran past its attainable accuracy restarts its search
 // direction), in three stages per iteration: the V-cycle (whose last kernel also forms r.z),
 // p' = z + beta p with the energy p'.G p', and r -= alpha G p' with G p' recomputed from p'
-// (never stored) and r.D^-1 r; x takes two iterations' steps every second iteration; small
-// per-column folds sum per-CTA partials in a fixed order (results are identical from run to
-// run).
+// (never stored) and r.D^-1 r; x takes two iterations' steps every second iteration.  The
+// direction and update passes stage their stencil operand per 32 x 4 node tile the same way.
+// Small per-column folds sum per-CTA partials in a fixed order (results are identical from
+// run to run).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -87,239 +90,6 @@ __device__ __forceinline__ float4 fma4(float s, float4 a, float4 c) {
     return make_float4(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y), fmaf(s, a.z, c.z), fmaf(s, a.w, c.w));
 }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-
-// (G v)_i in edge form, pad v_i + sum_j g_ij (v_i - v_j), for a field given by val(j) at the
-// node (x, y) of id i (coordinates passed in: no divisions here); with energy: also
-// pad v_i^2 + gE (v_i - v_E)^2 + gS (v_i - v_S)^2 + sum_TSV g (v_i - v_j)^2 / 2, whose sum over
-// all nodes is v^T G v with every edge counted once.
-template <bool ENERGY, class F>
-__device__ __forceinline__ float4 apply_g(const Lvl &L, int i, int x, int y, float4 c, float4 vi, F val,
-                                          float4 *energy) {
-    float4 acc = c.w * vi;
-    float4 en = zero4();
-    if constexpr (ENERGY) en = c.w * (vi * vi);
-    if (c.y != 0.f) {
-        const float4 d = vi - val(i + 1);
-        acc = fma4(c.y, d, acc);
-        if constexpr (ENERGY) en = fma4(c.y, d * d, en);
-    }
-    if (x > 0) {
-        const float g = L.coef[i - 1].y;
-        if (g != 0.f) acc = fma4(g, vi - val(i - 1), acc);
-    }
-    if (c.z != 0.f) {
-        const float4 d = vi - val(i + L.W);
-        acc = fma4(c.z, d, acc);
-        if constexpr (ENERGY) en = fma4(c.z, d * d, en);
-    }
-    if (y > 0) {
-        const float g = L.coef[i - L.W].z;
-        if (g != 0.f) acc = fma4(g, vi - val(i - L.W), acc);
-    }
-    if (c.x < 0.f) {
-        const int32_t e1 = L.tsv_ptr[i + 1];
-        for (int32_t e = L.tsv_ptr[i]; e < e1; ++e) {
-            const float g = L.tsv_g[e];
-            const float4 d = vi - val(L.tsv_nbr[e]);
-            acc = fma4(g, d, acc);
-            if constexpr (ENERGY) en = fma4(0.5f * g, d * d, en);
-        }
-    }
-    if constexpr (ENERGY) *energy = en;
-    return acc;
-}
-
-// The four children (dy, dx) of aggregate J = (t Hc + Y) Wc + X of the coarse level: node
-// ids, coefficients and the thread's 4 columns of r.  ok = the child exists and is not
-// floating (a floating node is not in P and has no conducting segment to the others).
-struct Quad {
-    int i[2][2];
-    bool ok[2][2];
-    float4 c[2][2], r[2][2];
-};
-
-__device__ __forceinline__ void load_quad(const Lvl &F, const float *r, int k, int col, int t, int Y, int X,
-                                          Quad &q) {
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-            const int x = 2 * X + dx, y = 2 * Y + dy;
-            const bool in = x < F.W && y < F.H;
-            const int i = in ? (t * F.H + y) * F.W + x : 0;
-            q.i[dy][dx] = i;
-            q.c[dy][dx] = in ? F.coef[i] : zero4();
-            q.ok[dy][dx] = in && q.c[dy][dx].x != 0.f;
-            q.r[dy][dx] = q.ok[dy][dx] ? f4ld(r + (int64_t)i * k + col) : zero4();
-        }
-}
-
-// (G v) at child (dy, dx) of a quad whose four children hold v[2][2]; ext(j, c_j, dJ) gives
-// v at a node outside the quad, whose coefficients are c_j and whose aggregate is J + dJ.
-template <class E>
-__device__ __forceinline__ float4 quad_g(const Lvl &F, const Quad &q, const float4 (&v)[2][2], int dy, int dx, int X,
-                                         int Y, int WcHc, int Wc, E ext) {
-    const float4 c = q.c[dy][dx];
-    const int i = q.i[dy][dx];
-    const float4 vi = v[dy][dx];
-    float4 acc = c.w * vi;
-    if (c.y != 0.f) {  // east: the sibling, or the first node of aggregate X + 1
-        const float4 nb = dx == 0 ? v[dy][1] : ext(i + 1, F.coef[i + 1], 1);
-        acc = fma4(c.y, vi - nb, acc);
-    }
-    if (2 * X + dx > 0) {  // west
-        float g;
-        float4 nb;
-        if (dx == 1) {
-            g = q.c[dy][0].y;
-            nb = v[dy][0];
-        } else {
-            const float4 cw = F.coef[i - 1];
-            g = cw.y;
-            nb = g != 0.f ? ext(i - 1, cw, -1) : zero4();
-        }
-        if (g != 0.f) acc = fma4(g, vi - nb, acc);
-    }
-    if (c.z != 0.f) {  // south
-        const float4 nb = dy == 0 ? v[1][dx] : ext(i + F.W, F.coef[i + F.W], Wc);
-        acc = fma4(c.z, vi - nb, acc);
-    }
-    if (2 * Y + dy > 0) {  // north
-        float g;
-        float4 nb;
-        if (dy == 1) {
-            g = q.c[0][dx].z;
-            nb = v[0][dx];
-        } else {
-            const float4 cn = F.coef[i - F.W];
-            g = cn.z;
-            nb = g != 0.f ? ext(i - F.W, cn, -Wc) : zero4();
-        }
-        if (g != 0.f) acc = fma4(g, vi - nb, acc);
-    }
-    if (c.x < 0.f) {  // TSV segments: same (x, y), the tier above or below
-        const int32_t e1 = F.tsv_ptr[i + 1];
-        for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
-            const int j = F.tsv_nbr[e];
-            acc = fma4(F.tsv_g[e], vi - ext(j, F.coef[j], j > i ? WcHc : -WcHc), acc);
-        }
-    }
-    return acc;
-}
-
-// per-CTA column partials in a fixed order: run[4] per thread -> part[chunk][col]
-__device__ __forceinline__ void block_partials(const Lay &l, int k, int cg, bool colok, const double (&acc)[4],
-                                               double *part) {
-    __shared__ double sred[256 * 4];
-    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) sred[(nl * l.TPN + cgl) * 4 + v] = colok ? acc[v] : 0.0;
-    __syncthreads();
-    if (threadIdx.x < l.TPN * 4) {
-        const int c = threadIdx.x / 4, v = threadIdx.x % 4;
-        double s = 0.0;
-        for (int q = 0; q < l.NPS; ++q) s += sred[(q * l.TPN + c) * 4 + v];
-        const int col = (blockIdx.y * l.TPN + c) * 4 + v;
-        if (col < k) part[(int64_t)blockIdx.x * k + col] = s;
-    }
-    (void)cg;
-}
-
-// ---- V-cycle kernels ----------------------------------------------------------------
-
-// restriction of the pre-smoothed residual: rc[J] = sum over the fine children i of J of
-// (r - G z0)_i with z0 = w D^-1 r (z0 is recomputed, never stored).  A thread owns one
-// aggregate and 4 columns: the children's values come from registers, only the 8 nodes
-// around the quad (and TSV partners) are read from memory.
-__global__ void __launch_bounds__(256) k_mg_down(Lvl F, Lvl C, int k, Lay l, const float *__restrict__ r,
-                                                 float *__restrict__ rc) {
-    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
-    const int cg = blockIdx.y * l.TPN + cgl;
-    if (cg >= l.KG) return;
-    const int col = cg * 4;
-    const int Wc = C.W, WcHc = C.W * C.H;
-    auto ext = [&](int j, float4 cj, int) { return (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col); };
-    const int J0 = blockIdx.x * l.NPS * l.steps + nl;
-    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
-    for (int J = J0; J < J1; J += l.NPS) {
-        const int X = J % Wc, Y = (J / Wc) % C.H, t = J / WcHc;
-        Quad q;
-        load_quad(F, r, k, col, t, Y, X, q);
-        float4 z0[2][2];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) z0[dy][dx] = (kOmega * fabsf(q.c[dy][dx].x)) * q.r[dy][dx];
-        float4 acc = zero4();
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx)
-                if (q.ok[dy][dx]) acc = acc + (q.r[dy][dx] - quad_g(F, q, z0, dy, dx, X, Y, WcHc, Wc, ext));
-        f4st(rc + (int64_t)J * k + col, acc);
-    }
-}
-
-// prolongation, over-correction and post-sweep on a level, one thread per coarse aggregate
-// and 4 columns: v = z0 + s P zc on the four children, then z = v + w D^-1 (r - G v); with
-// DOT the CTA also writes its partials of r.z
-template <bool DOT>
-__global__ void __launch_bounds__(256, 3) k_mg_up(Lvl F, Lvl C, int k, Lay l, const float *__restrict__ r,
-                                               const float *__restrict__ zc, float *__restrict__ z, double *part) {
-    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
-    const int cg = blockIdx.y * l.TPN + cgl;
-    const bool colok = cg < l.KG;
-    const int col = colok ? cg * 4 : 0;
-    const int Wc = C.W, WcHc = C.W * C.H;
-    float run[4] = {0.f, 0.f, 0.f, 0.f};
-    const int J0 = blockIdx.x * l.NPS * l.steps + nl;
-    const int J1 = (int)min(C.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
-    if (colok) {
-        for (int J = J0; J < J1; J += l.NPS) {
-            const int X = J % Wc, Y = (J / Wc) % C.H, t = J / WcHc;
-            auto ext = [&](int j, float4 cj, int dJ) {
-                return fma4(kScale, f4ld(zc + (int64_t)(J + dJ) * k + col),
-                            (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col));
-            };
-            Quad q;
-            load_quad(F, r, k, col, t, Y, X, q);
-            const float4 zcJ = f4ld(zc + (int64_t)J * k + col);
-            float4 v[2][2];
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx)
-                    v[dy][dx] = q.ok[dy][dx] ? fma4(kScale, zcJ, (kOmega * fabsf(q.c[dy][dx].x)) * q.r[dy][dx])
-                                             : zero4();
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int x = 2 * X + dx, y = 2 * Y + dy;
-                    if (x >= F.W || y >= F.H) continue;
-                    float4 out = zero4();
-                    if (q.ok[dy][dx]) {
-                        const float4 ri = q.r[dy][dx];
-                        out = fma4(kOmega * fabsf(q.c[dy][dx].x),
-                                   ri - quad_g(F, q, v, dy, dx, X, Y, WcHc, Wc, ext), v[dy][dx]);
-                        if constexpr (DOT) {
-                            run[0] = fmaf(ri.x, out.x, run[0]);
-                            run[1] = fmaf(ri.y, out.y, run[1]);
-                            run[2] = fmaf(ri.z, out.z, run[2]);
-                            run[3] = fmaf(ri.w, out.w, run[3]);
-                        }
-                    }
-                    f4st(z + (int64_t)q.i[dy][dx] * k + col, out);
-                }
-        }
-    }
-    if constexpr (DOT) {
-        double acc[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = (double)run[v];
-        block_partials(l, k, cg, colok, acc, part);
-    }
-}
 
 // ---- TMA-tiled restriction and prolongation ------------------------------------------------
 //
@@ -526,10 +296,228 @@ __global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtenso
     }
 }
 
+// ---- TMA-tiled CG passes on the finest level ---------------------------------------------
+//
+// A CTA owns 32 x 4 nodes of one tier and 32 RHS columns; the operands that the stencil needs
+// at neighbours are staged by cp.async.bulk.tensor with a one-node halo (zero fill at the mesh
+// edge): the direction pass loads z and p over x0..x0+32, y0..y0+4 (east and south halo only:
+// its energy form needs those two neighbours), the update pass loads p' over x0-1..x0+32,
+// y0-1..y0+4.  Operands needed only at the node itself (r, x, p'_prev) are plain coalesced
+// float4 loads.  Items: (node, group of 4 columns), 8 column groups of 4 nodes per warp.
+
+constexpr int CX = 32, CY = 4;                     // interior nodes per tile
+constexpr int SPX = CX + 1, SPY = CY + 1;          // direction pass: east/south halo
+constexpr int UPX = CX + 2, UPY = CY + 2;          // update pass: halo on every side
+constexpr int S_V = SPY * SPX * TCB * 4;           // 21,120 bytes per vector
+constexpr int S_C = ((SPY * SPX * 16 + 127) / 128) * 128;
+constexpr int S_SMEM = 2 * S_V + S_C + 128;
+constexpr int U_V = UPY * UPX * TCB * 4;           // 26,112 bytes
+constexpr int U_C = ((UPY * UPX * 16 + 127) / 128) * 128;
+constexpr int U_SMEM = U_V + U_C + 128;
+
+int64_t n_ctiles(const Lvl &F) { return (int64_t)((F.W + CX - 1) / CX) * ((F.H + CY - 1) / CY) * F.T; }
+dim3 ctile_grid(const Lvl &F, int k) { return dim3((unsigned)n_ctiles(F), (unsigned)((k + TCB - 1) / TCB)); }
+
+// issue loads (thread 0), then a bounded, CTA-uniform wait
+__device__ __forceinline__ bool ctile_wait(uint64_t *bar, int *err) {
+    bool done = true;
+    for (uint32_t spins = 0; !mg_try_wait(bar, 0);) {
+        if (++spins > kTileSpin) {
+            done = false;
+            break;
+        }
+    }
+    if (__syncthreads_and(done ? 1 : 0)) return true;
+    if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar, 0); ++q) {
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bar_init_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mg_saddr(bar)), "r"(bytes) : "memory");
+}
+
+struct CGeo {
+    int x0, y0, t, c0;
+};
+__device__ __forceinline__ CGeo ctile_geo(const Lvl &F) {
+    const int tx = (F.W + CX - 1) / CX, ty = (F.H + CY - 1) / CY;
+    CGeo g;
+    int b = blockIdx.x;
+    g.x0 = (b % tx) * CX;
+    b /= tx;
+    g.y0 = (b % ty) * CY;
+    g.t = b / ty;
+    g.c0 = blockIdx.y * TCB;
+    return g;
+}
+
+// per column: the items of the CTA that share it (thread q holds 4 columns of group q % 8),
+// summed in a fixed order
+__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, double *part) {
+    __shared__ double sred[256 * 4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sred[threadIdx.x * 4 + v] = (double)run[v];
+    __syncthreads();
+    if (threadIdx.x < TCB) {
+        const int cg = threadIdx.x >> 2, v = threadIdx.x & 3;
+        double acc = 0.0;
+        for (int q = cg; q < 256; q += 8) acc += sred[q * 4 + v];
+        const int col = c0 + threadIdx.x;
+        if (col < k) part[(int64_t)blockIdx.x * k + col] = acc;
+    }
+}
+
+// p' = z + beta p over the tile; partials of p'.G p' in edge form (pad, east, south, half TSV)
+__global__ void __launch_bounds__(256) k_mg_dir_tile(const __grid_constant__ CUtensorMap mzt,
+                                                     const __grid_constant__ CUtensorMap mpt,
+                                                     const __grid_constant__ CUtensorMap mct, Lvl F, int k,
+                                                     const float *__restrict__ z, const float *__restrict__ p,
+                                                     const double *__restrict__ beta, float *__restrict__ p_out,
+                                                     double *part, int *err) {
+    extern __shared__ unsigned char mg_dir_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char *sm = mg_dir_raw + ((128u - (mg_saddr(mg_dir_raw) & 127u)) & 127u);
+    const float *zs = reinterpret_cast<const float *>(sm);
+    const float *ps = reinterpret_cast<const float *>(sm + S_V);
+    const float4 *cs = reinterpret_cast<const float4 *>(sm + 2 * S_V);
+    const CGeo g = ctile_geo(F);
+    if (threadIdx.x == 0) {
+        bar_init_expect(&bar, (uint32_t)(2 * S_V + SPY * SPX * 16));
+        mg_tma4(sm, &mzt, &bar, g.c0, g.x0, g.y0, g.t);
+        mg_tma4(sm + S_V, &mpt, &bar, g.c0, g.x0, g.y0, g.t);
+        mg_tma4(sm + 2 * S_V, &mct, &bar, 0, g.x0, g.y0, g.t);
+    }
+    __syncthreads();
+    if (!ctile_wait(&bar, err)) return;
+    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    const int cg = threadIdx.x & 7;
+    const int col = g.c0 + cg * 4;
+    const float4 b4 = col < k ? make_float4((float)beta[col], (float)beta[col + 1], (float)beta[col + 2],
+                                            (float)beta[col + 3])
+                              : zero4();
+    auto sv = [&](int ly, int lx) {
+        const int o = (ly * SPX + lx) * TCB + cg * 4;
+        return (b4 * *reinterpret_cast<const float4 *>(ps + o)) + *reinterpret_cast<const float4 *>(zs + o);
+    };
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int node = (threadIdx.x >> 3) + 32 * h;  // 0 .. 127
+        const int lx = node % CX, ly = node / CX;
+        const int x = g.x0 + lx, y = g.y0 + ly;
+        if (x >= F.W || y >= F.H || col >= k) continue;
+        const int i = (g.t * F.H + y) * F.W + x;
+        const float4 c = cs[ly * SPX + lx];
+        float4 pv = zero4();
+        if (c.x != 0.f) {
+            pv = sv(ly, lx);
+            float4 en = c.w * (pv * pv);
+            if (c.y != 0.f) {
+                const float4 d = pv - sv(ly, lx + 1);
+                en = fma4(c.y, d * d, en);
+            }
+            if (c.z != 0.f) {
+                const float4 d = pv - sv(ly + 1, lx);
+                en = fma4(c.z, d * d, en);
+            }
+            if (c.x < 0.f) {
+                const int32_t e1 = F.tsv_ptr[i + 1];
+                for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
+                    const int64_t oj = (int64_t)F.tsv_nbr[e] * k + col;
+                    const float4 d = pv - ((b4 * f4ld(p + oj)) + f4ld(z + oj));
+                    en = fma4(0.5f * F.tsv_g[e], d * d, en);
+                }
+            }
+            run[0] += en.x; run[1] += en.y; run[2] += en.z; run[3] += en.w;
+        }
+        f4st(p_out + (int64_t)i * k + col, pv);
+    }
+    ctile_partials(run, k, g.c0, part);
+}
+
+// r -= alpha G p' with G p' from the staged p' tile; partials of r.D^-1 r; with XPAIR also
+// x += alpha_prev p'_prev + alpha p'
+template <bool XPAIR>
+__global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUtensorMap mpt,
+                                                     const __grid_constant__ CUtensorMap mct, Lvl F, int k,
+                                                     const double *__restrict__ alpha,
+                                                     const double *__restrict__ alpha_prev,
+                                                     const float *__restrict__ p, const float *__restrict__ p_prev,
+                                                     float *__restrict__ x, float *__restrict__ r, double *part,
+                                                     int *err) {
+    extern __shared__ unsigned char mg_upd_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char *sm = mg_upd_raw + ((128u - (mg_saddr(mg_upd_raw) & 127u)) & 127u);
+    const float *ps = reinterpret_cast<const float *>(sm);
+    const float4 *cs = reinterpret_cast<const float4 *>(sm + U_V);
+    const CGeo g = ctile_geo(F);
+    if (threadIdx.x == 0) {
+        bar_init_expect(&bar, (uint32_t)(U_V + UPY * UPX * 16));
+        mg_tma4(sm, &mpt, &bar, g.c0, g.x0 - 1, g.y0 - 1, g.t);
+        mg_tma4(sm + U_V, &mct, &bar, 0, g.x0 - 1, g.y0 - 1, g.t);
+    }
+    __syncthreads();
+    if (!ctile_wait(&bar, err)) return;
+    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    const int cg = threadIdx.x & 7;
+    const int col = g.c0 + cg * 4;
+    auto ld4d = [&](const double *a) {
+        return col < k ? make_float4((float)a[col], (float)a[col + 1], (float)a[col + 2], (float)a[col + 3]) : zero4();
+    };
+    const float4 a4 = ld4d(alpha);
+    const float4 ap4 = XPAIR ? ld4d(alpha_prev) : zero4();
+    auto pv_at = [&](int ly, int lx) {
+        return *reinterpret_cast<const float4 *>(ps + (ly * UPX + lx) * TCB + cg * 4);
+    };
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int node = (threadIdx.x >> 3) + 32 * h;
+        const int lx0 = node % CX, ly0 = node / CX;
+        const int xg = g.x0 + lx0, yg = g.y0 + ly0;
+        if (xg >= F.W || yg >= F.H || col >= k) continue;
+        const int lx = lx0 + 1, ly = ly0 + 1;
+        const int i = (g.t * F.H + yg) * F.W + xg;
+        const float4 c = cs[ly * UPX + lx];
+        if (c.x == 0.f) continue;  // floating: r, x and p' stay 0
+        const float4 pv = pv_at(ly, lx);
+        float4 q = c.w * pv;
+        if (c.y != 0.f) q = fma4(c.y, pv - pv_at(ly, lx + 1), q);
+        {
+            const float gw = cs[ly * UPX + lx - 1].y;
+            if (gw != 0.f) q = fma4(gw, pv - pv_at(ly, lx - 1), q);
+        }
+        if (c.z != 0.f) q = fma4(c.z, pv - pv_at(ly + 1, lx), q);
+        {
+            const float gn = cs[(ly - 1) * UPX + lx].z;
+            if (gn != 0.f) q = fma4(gn, pv - pv_at(ly - 1, lx), q);
+        }
+        if (c.x < 0.f) {
+            const int32_t e1 = F.tsv_ptr[i + 1];
+            for (int32_t e = F.tsv_ptr[i]; e < e1; ++e)
+                q = fma4(F.tsv_g[e], pv - f4ld(p + (int64_t)F.tsv_nbr[e] * k + col), q);
+        }
+        const int64_t o = (int64_t)i * k + col;
+        const float4 rv = f4ld(r + o) - a4 * q;
+        f4st(r + o, rv);
+        if constexpr (XPAIR) f4st(x + o, f4ld(x + o) + ap4 * f4ld(p_prev + o) + a4 * pv);
+        const float di = fabsf(c.x);
+        run[0] = fmaf(di * rv.x, rv.x, run[0]);
+        run[1] = fmaf(di * rv.y, rv.y, run[1]);
+        run[2] = fmaf(di * rv.z, rv.z, run[2]);
+        run[3] = fmaf(di * rv.w, rv.w, run[3]);
+    }
+    ctile_partials(run, k, g.c0, part);
+}
+
 // coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
 // zero rows and columns at floating nodes) computed once on the host; one thread per node and
 // 4 columns, the inverse's row i read once per thread, r's rows shared through L1/L2
-__global__ void __launch_bounds__(256) k_mg_cinv(int n, int k, Lay l, const float *__restrict__ ainv,
+__global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, Lay l, const float *__restrict__ ainv,
                                                  const float *__restrict__ r, float *__restrict__ z) {
     const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
     const int cg = blockIdx.y * l.TPN + cgl;
@@ -538,99 +526,19 @@ __global__ void __launch_bounds__(256) k_mg_cinv(int n, int k, Lay l, const floa
     const int i0 = blockIdx.x * l.NPS * l.steps + nl;
     const int i1 = min(n, (blockIdx.x + 1) * l.NPS * l.steps);
     for (int i = i0; i < i1; i += l.NPS) {
-        const float *row = ainv + (int64_t)i * n;
-        float4 a0 = zero4(), a1 = zero4();
-        int j = 0;
-        for (; j + 1 < n; j += 2) {
-            a0 = fma4(row[j], f4ld(r + (int64_t)j * k + col), a0);
-            a1 = fma4(row[j + 1], f4ld(r + (int64_t)(j + 1) * k + col), a1);
+        const float4 *row = reinterpret_cast<const float4 *>(ainv + (int64_t)i * ld);  // ld % 4 == 0, zero padded
+        float4 a0 = zero4(), a1 = zero4(), a2 = zero4(), a3 = zero4();
+#pragma unroll 4
+        for (int j4 = 0; j4 < ld / 4; ++j4) {
+            const float4 w = row[j4];
+            const int64_t o = (int64_t)(4 * j4) * k + col;
+            a0 = fma4(w.x, f4ld(r + o), a0);
+            a1 = fma4(w.y, f4ld(r + o + k), a1);
+            a2 = fma4(w.z, f4ld(r + o + 2 * k), a2);
+            a3 = fma4(w.w, f4ld(r + o + 3 * k), a3);
         }
-        if (j < n) a0 = fma4(row[j], f4ld(r + (int64_t)j * k + col), a0);
-        f4st(z + (int64_t)i * k + col, a0 + a1);
+        f4st(z + (int64_t)i * k + col, (a0 + a1) + (a2 + a3));
     }
-}
-
-// ---- CG kernels (fine level) ----------------------------------------------------------
-
-// p' = z + beta p; partials of p'.G p' (edge energy).  q = G p' is not stored: the update
-// pass recomputes it from p' (a stencil on FP32 costs less than a vector round trip).
-__global__ void __launch_bounds__(256) k_mg_spmv(Lvl F, int k, Lay l, const float *__restrict__ z,
-                                                 const float *__restrict__ p, const double *__restrict__ beta,
-                                                 float *__restrict__ p_out, double *part) {
-    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
-    const int cg = blockIdx.y * l.TPN + cgl;
-    const bool colok = cg < l.KG;
-    const int col = colok ? cg * 4 : 0;
-    const float4 b4 = colok ? make_float4((float)beta[col], (float)beta[col + 1], (float)beta[col + 2],
-                                          (float)beta[col + 3])
-                            : zero4();
-    auto val = [&](int j) {
-        const int64_t o = (int64_t)j * k + col;
-        return (b4 * f4ld(p + o)) + f4ld(z + o);
-    };
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    float run[4] = {0.f, 0.f, 0.f, 0.f};
-    const int i0 = blockIdx.x * l.NPS * l.steps + nl;
-    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
-    if (colok) {
-        for (int i = i0; i < i1; i += l.NPS) {
-            const float4 c = F.coef[i];
-            float4 pv = zero4();
-            if (c.x != 0.f) {
-                pv = val(i);
-                float4 en;
-                (void)apply_g<true>(F, i, i % F.W, (i / F.W) % F.H, c, pv, val, &en);
-                run[0] += en.x; run[1] += en.y; run[2] += en.z; run[3] += en.w;
-            }
-            f4st(p_out + (int64_t)i * k + col, pv);
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[v] = (double)run[v];
-    block_partials(l, k, cg, colok, acc, part);
-}
-
-// r -= alpha G p' (G p' recomputed from p'); partials of r.D^-1 r.  With XPAIR (every second
-// iteration) also x += alpha_prev p'_prev + alpha p': x takes two iterations' steps at once.
-template <bool XPAIR>
-__global__ void __launch_bounds__(256) k_mg_update(Lvl F, int k, Lay l, const double *__restrict__ alpha,
-                                                   const double *__restrict__ alpha_prev, const float *__restrict__ p,
-                                                   const float *__restrict__ p_prev, float *__restrict__ x,
-                                                   float *__restrict__ r, double *part) {
-    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
-    const int cg = blockIdx.y * l.TPN + cgl;
-    const bool colok = cg < l.KG;
-    const int col = colok ? cg * 4 : 0;
-    auto ld4d = [&](const double *a) {
-        return colok ? make_float4((float)a[col], (float)a[col + 1], (float)a[col + 2], (float)a[col + 3]) : zero4();
-    };
-    const float4 a4 = ld4d(alpha);
-    const float4 ap4 = XPAIR ? ld4d(alpha_prev) : zero4();
-    auto val = [&](int j) { return f4ld(p + (int64_t)j * k + col); };
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    float run[4] = {0.f, 0.f, 0.f, 0.f};
-    const int i0 = blockIdx.x * l.NPS * l.steps + nl;
-    const int i1 = (int)min(F.n, (int64_t)(blockIdx.x + 1) * l.NPS * l.steps);
-    if (colok) {
-        for (int i = i0; i < i1; i += l.NPS) {
-            const int64_t o = (int64_t)i * k + col;
-            const float4 c = F.coef[i];
-            if (c.x == 0.f) continue;  // floating: r, x and p' stay 0
-            const float4 pv = f4ld(p + o);
-            const float4 qv = apply_g<false>(F, i, i % F.W, (i / F.W) % F.H, c, pv, val, nullptr);
-            const float4 rv = f4ld(r + o) - a4 * qv;
-            f4st(r + o, rv);
-            if constexpr (XPAIR) f4st(x + o, f4ld(x + o) + ap4 * f4ld(p_prev + o) + a4 * pv);
-            const float di = fabsf(c.x);
-            run[0] = fmaf(di * rv.x, rv.x, run[0]);
-            run[1] = fmaf(di * rv.y, rv.y, run[1]);
-            run[2] = fmaf(di * rv.z, rv.z, run[2]);
-            run[3] = fmaf(di * rv.w, rv.w, run[3]);
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[v] = (double)run[v];
-    block_partials(l, k, cg, colok, acc, part);
 }
 
 // ---- per-column folds (one CTA per column, partials summed in a fixed tree order) -------
@@ -739,10 +647,14 @@ struct MgHier {
     std::vector<er_grid *> grids;  // level l >= 1; grids[0] = nullptr (the fine grid)
     std::vector<Lvl> lv;
     std::vector<float *> r, z;     // per level [n][k]; r[0] is the CG residual (not owned)
-    float *ainv = nullptr;         // dense inverse of the coarsest level [n_c][n_c]
+    float *ainv = nullptr;         // dense inverse of the coarsest level [n_c][ld_inv], zero padded
+    int ld_inv = 0;                // row stride of ainv: n_c rounded up to a multiple of 4
     double *msc = nullptr;         // per column: recursive residual, previous alpha [2][k]
     // tiled kernels, per level l: r_l (finer side), coefficients, z_l (coarser side of l - 1)
     std::vector<CUtensorMap> map_r, map_c, map_z;
+    // tiled CG passes on the finest level: direction (z, p[0], p[1], coefficients; east/south
+    // halo) and update (p[0], p[1], coefficients; halo on every side)
+    CUtensorMap dmap_z, dmap_p[2], dmap_c, umap_p[2], umap_c;
     double *part = nullptr;
     int64_t part_chunks = 0;
     int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
@@ -941,8 +853,13 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
             free_mg(&g);
             return ist;
         }
-        ER_CUDA(cudaMalloc(&h->ainv, inv.size() * sizeof(float)));
-        ER_CUDA(cudaMemcpy(h->ainv, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice));
+        const int nc = (int)cur->n;
+        h->ld_inv = (nc + 3) & ~3;
+        std::vector<float> padded((size_t)nc * h->ld_inv, 0.0f);
+        for (int a = 0; a < nc; ++a)
+            std::memcpy(&padded[(size_t)a * h->ld_inv], &inv[(size_t)a * nc], (size_t)nc * sizeof(float));
+        ER_CUDA(cudaMalloc(&h->ainv, padded.size() * sizeof(float)));
+        ER_CUDA(cudaMemcpy(h->ainv, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
         ER_CUDA(cudaMalloc(&h->cnt, 2 * sizeof(int)));
         ER_CUDA(cudaMallocHost(&h->h_cnt, 2 * sizeof(int)));
     }
@@ -955,11 +872,16 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
         h->part = nullptr;
         h->k = 0;
         for (size_t l = 0; l < h->lv.size(); ++l) {
+            // the coarsest level's r has ld_inv rows; rows n_c .. ld_inv - 1 stay zero
+            const int64_t rows = l + 1 == h->lv.size() ? h->ld_inv : h->lv[l].n;
             const size_t bytes = (size_t)h->lv[l].n * k * sizeof(float);
-            if (l > 0) ER_CUDA(cudaMalloc(&h->r[l], bytes));
+            if (l > 0) {
+                ER_CUDA(cudaMalloc(&h->r[l], (size_t)rows * k * sizeof(float)));
+                ER_CUDA(cudaMemset(h->r[l], 0, (size_t)rows * k * sizeof(float)));
+            }
             ER_CUDA(cudaMalloc(&h->z[l], bytes));
         }
-        h->part_chunks = std::max(make_lay(g.n, k).chunks, n_tiles(h->lv[1]));
+        h->part_chunks = std::max(std::max(make_lay(g.n, k).chunks, n_tiles(h->lv[1])), n_ctiles(h->lv[0]));
         if (h->msc) cudaFree(h->msc);
         ER_CUDA(cudaMalloc(&h->msc, (size_t)2 * k * sizeof(double)));
         ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(double)));
@@ -1020,7 +942,7 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     }
     const Lvl &C = h.lv[L - 1];
     const Lay lco = make_lay(C.n, k);
-    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, dim3((unsigned)lco.chunks, lco.ncb), 0, (int)C.n, k, lco,
+    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, dim3((unsigned)lco.chunks, lco.ncb), 0, (int)C.n, h.ld_inv, k, lco,
               (const float *)h.ainv, (const float *)h.r[L - 1], h.z[L - 1]);
     for (int l = L - 2; l >= 0; --l) {
         const float *rl = l == 0 ? r0 : h.r[l];
@@ -1044,20 +966,22 @@ int mg_iterate(const MgRun &m, int cur, Prof *pf) {
     const int k = m.k;
     float *r = (float *)w.r[0];
     vcycle(m, r, pf);
-    const Lay lf = make_lay(m.g->n, k);
-    const dim3 grid((unsigned)lf.chunks, lf.ncb);
-    mg_launch(w, pf, ER_PASS_A, k_mg_spmv, grid, 0, h.lv[0], k, lf, (const float *)h.z[0], (const float *)w.p[cur],
-              (const double *)(w.scal + k), (float *)w.p[1 - cur], h.part);
-    mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_ALPHA>, dim3((unsigned)k), 0, fold_args(m, lf.chunks));
+    const Lvl &L0 = h.lv[0];
+    const dim3 grid = ctile_grid(L0, k);
+    const int64_t nct = n_ctiles(L0);
+    mg_launch(w, pf, ER_PASS_A, k_mg_dir_tile, grid, S_SMEM, h.dmap_z, h.dmap_p[cur], h.dmap_c, L0, k,
+              (const float *)h.z[0], (const float *)w.p[cur], (const double *)(w.scal + k), (float *)w.p[1 - cur],
+              h.part, m.err);
+    mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_ALPHA>, dim3((unsigned)k), 0, fold_args(m, nct));
     if (cur == 1)  // second iteration of a pair: x += alpha_prev p'_prev + alpha p'
-        mg_launch(w, pf, ER_PASS_B, k_mg_update<true>, grid, 0, h.lv[0], k, lf, (const double *)w.scal,
-                  (const double *)(h.msc + k), (const float *)w.p[1 - cur], (const float *)w.p[cur], (float *)m.Z, r,
-                  h.part);
+        mg_launch(w, pf, ER_PASS_B, k_mg_upd_tile<true>, grid, U_SMEM, h.umap_p[1 - cur], h.umap_c, L0, k,
+                  (const double *)w.scal, (const double *)(h.msc + k), (const float *)w.p[1 - cur],
+                  (const float *)w.p[cur], (float *)m.Z, r, h.part, m.err);
     else
-        mg_launch(w, pf, ER_PASS_B0, k_mg_update<false>, grid, 0, h.lv[0], k, lf, (const double *)w.scal,
-                  (const double *)(h.msc + k), (const float *)w.p[1 - cur], (const float *)w.p[cur], (float *)m.Z, r,
-                  h.part);
-    mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_RR>, dim3((unsigned)k), 0, fold_args(m, lf.chunks));
+        mg_launch(w, pf, ER_PASS_B0, k_mg_upd_tile<false>, grid, U_SMEM, h.umap_p[1 - cur], h.umap_c, L0, k,
+                  (const double *)w.scal, (const double *)(h.msc + k), (const float *)w.p[1 - cur],
+                  (const float *)w.p[cur], (float *)m.Z, r, h.part, m.err);
+    mg_launch(w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_RR>, dim3((unsigned)k), 0, fold_args(m, nct));
     return 1 - cur;
 }
 
@@ -1082,11 +1006,23 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
             if (ms == ER_OK) ms = mg_map(&h->map_z[l], h->z[l], k, h->lv[l], TCB, TZX, TZY);
             if (ms != ER_OK) return ms;
         }
+        const Lvl &L0 = h->lv[0];
+        er_status ms = mg_map(&h->dmap_z, h->z[0], k, L0, TCB, SPX, SPY);
+        for (int b = 0; b < 2 && ms == ER_OK; ++b) {
+            ms = mg_map(&h->dmap_p[b], w.p[b], k, L0, TCB, SPX, SPY);
+            if (ms == ER_OK) ms = mg_map(&h->umap_p[b], w.p[b], k, L0, TCB, UPX, UPY);
+        }
+        if (ms == ER_OK) ms = mg_map(&h->dmap_c, L0.coef, 4, L0, 4, SPX, SPY);
+        if (ms == ER_OK) ms = mg_map(&h->umap_c, L0.coef, 4, L0, 4, UPX, UPY);
+        if (ms != ER_OK) return ms;
         static bool attr = false;
         if (!attr) {
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_dir_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
             attr = true;
         }
     }
