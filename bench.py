@@ -772,7 +772,7 @@ def run_ours(args, rank, world, local_rank):
     mg = prec == "fp32" and args.precond == "mg"
     opts.precond = 1 if mg else 0
     if mg:
-        opts.check_every = 4  # a V-cycle iteration costs ~4 stencil passes: poll sooner
+        opts.check_every = 2  # a multigrid iteration costs several stencil passes: poll sooner
     opts.profile = 1
     stream = torch.cuda.current_stream()
 
@@ -820,11 +820,11 @@ def run_ours(args, rank, world, local_rank):
         # reads r and writes r_1 (n/4 rows); the post-sweep reads r and z_1 and writes z.  The
         # coarse levels together (pass kind 5, one entry per V-cycle) move 3.5 n_l k s per level,
         # n_l = n / 4^l for l >= 1, a factor 1/3 of the finest level's 3.5 n k s.
-        kinds = [(1, "k_mg_update<true>", 6 * nk * es + coef),      # p', r, x, p'_prev in; r, x out
-                 (4, "k_mg_update<false>", 3 * nk * es + coef),     # p', r in; r out
-                 (0, "k_mg_spmv", 3 * nk * es + coef),              # z, p in; p' out
-                 (7, "k_mg_up<true> (finest level)", int(2.25 * nk * es) + coef),
-                 (6, "k_mg_down (finest level)", int(1.25 * nk * es) + coef),
+        kinds = [(1, "k_mg_upd_tile<true>", 6 * nk * es + coef),    # p', r, x, p'_prev in; r, x out
+                 (4, "k_mg_upd_tile<false>", 3 * nk * es + coef),   # p', r in; r out
+                 (0, "k_mg_dir_tile", 3 * nk * es + coef),          # z, p in; p' out
+                 (7, "k_mg_tile<true, true> (finest level)", int(2.25 * nk * es) + coef),
+                 (6, "k_mg_tile<false, false> (finest level)", int(1.25 * nk * es) + coef),
                  (5, "V-cycle on the coarse levels", int(3.5 * nk * es / 3))]
     elif prec == "fp32":
         # (pass kind index, kernel, algorithmic bytes per launch)
