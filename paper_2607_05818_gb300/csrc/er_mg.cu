@@ -117,7 +117,7 @@ int64_t n_tiles(const Lvl &C) {
     return (int64_t)((C.W + TAX - 1) / TAX) * ((C.H + TAY - 1) / TAY) * C.T;
 }
 
-dim3 tile_grid(const Lvl &C, int k) { return dim3((unsigned)n_tiles(C), (unsigned)((k + TCB - 1) / TCB)); }
+dim3 tile_grid(const Lvl &C, int k) { return dim3((unsigned)(n_tiles(C) * ((k + TCB - 1) / TCB))); }
 
 __device__ __forceinline__ uint32_t mg_saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -176,15 +176,20 @@ struct TileGeo {
     int X0, Y0, t, c0;
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const Lvl &C) {
+// Block -> (tile, column block).  The column blocks of one tile are adjacent in launch order, so
+// the CTAs that read the same node rows (each takes a 128-byte slice of them) run together and
+// the L2's 256-byte fills are used by both neighbours.
+__device__ __forceinline__ TileGeo tile_geo(const Lvl &C, int k, int &tile) {
+    const int ncb = (k + TCB - 1) / TCB;
     const int tx = (C.W + TAX - 1) / TAX, ty = (C.H + TAY - 1) / TAY;
     TileGeo g;
-    int b = blockIdx.x;
+    int b = blockIdx.x / ncb;
+    tile = b;
+    g.c0 = (blockIdx.x % ncb) * TCB;
     g.X0 = (b % tx) * TAX;
     b /= tx;
     g.Y0 = (b % ty) * TAY;
     g.t = b / ty;
-    g.c0 = blockIdx.y * TCB;
     return g;
 }
 
@@ -201,7 +206,8 @@ __global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtenso
     const float *rs = reinterpret_cast<const float *>(sm);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + T_R);
     const float *zs = reinterpret_cast<const float *>(sm + T_R + T_C);
-    const TileGeo g = tile_geo(C);
+    int tile;
+    const TileGeo g = tile_geo(C, k, tile);
     const bool ok = tile_load(sm, &bar, &mr, &mc, UP ? &mz : nullptr, g.c0, g.X0, g.Y0, g.t, err);
     if (!ok) return;
     const int Wc = C.W, WcHc = C.W * C.H;
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtenso
             double sacc = 0.0;
             for (int q = cg; q < 256; q += 8) sacc += sred[q * 4 + v];
             const int col = g.c0 + threadIdx.x;
-            if (col < k) part[(int64_t)blockIdx.x * k + col] = sacc;
+            if (col < k) part[(int64_t)tile * k + col] = sacc;
         }
     }
 }
@@ -316,7 +322,7 @@ constexpr int U_C = ((UPY * UPX * 16 + 127) / 128) * 128;
 constexpr int U_SMEM = U_V + U_C + 128;
 
 int64_t n_ctiles(const Lvl &F) { return (int64_t)((F.W + CX - 1) / CX) * ((F.H + CY - 1) / CY) * F.T; }
-dim3 ctile_grid(const Lvl &F, int k) { return dim3((unsigned)n_ctiles(F), (unsigned)((k + TCB - 1) / TCB)); }
+dim3 ctile_grid(const Lvl &F, int k) { return dim3((unsigned)(n_ctiles(F) * ((k + TCB - 1) / TCB))); }
 
 // issue loads (thread 0), then a bounded, CTA-uniform wait
 __device__ __forceinline__ bool ctile_wait(uint64_t *bar, int *err) {
@@ -345,21 +351,23 @@ __device__ __forceinline__ void bar_init_expect(uint64_t *bar, uint32_t bytes) {
 struct CGeo {
     int x0, y0, t, c0;
 };
-__device__ __forceinline__ CGeo ctile_geo(const Lvl &F) {
+__device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int &tile) {  // column block fastest
+    const int ncb = (k + TCB - 1) / TCB;
     const int tx = (F.W + CX - 1) / CX, ty = (F.H + CY - 1) / CY;
     CGeo g;
-    int b = blockIdx.x;
+    int b = blockIdx.x / ncb;
+    tile = b;
+    g.c0 = (blockIdx.x % ncb) * TCB;
     g.x0 = (b % tx) * CX;
     b /= tx;
     g.y0 = (b % ty) * CY;
     g.t = b / ty;
-    g.c0 = blockIdx.y * TCB;
     return g;
 }
 
 // per column: the items of the CTA that share it (thread q holds 4 columns of group q % 8),
 // summed in a fixed order
-__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, double *part) {
+__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, int tile, double *part) {
     __shared__ double sred[256 * 4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) sred[threadIdx.x * 4 + v] = (double)run[v];
@@ -369,7 +377,7 @@ __device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int
         double acc = 0.0;
         for (int q = cg; q < 256; q += 8) acc += sred[q * 4 + v];
         const int col = c0 + threadIdx.x;
-        if (col < k) part[(int64_t)blockIdx.x * k + col] = acc;
+        if (col < k) part[(int64_t)tile * k + col] = acc;
     }
 }
 
@@ -386,7 +394,8 @@ __global__ void __launch_bounds__(256) k_mg_dir_tile(const __grid_constant__ CUt
     const float *zs = reinterpret_cast<const float *>(sm);
     const float *ps = reinterpret_cast<const float *>(sm + S_V);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + 2 * S_V);
-    const CGeo g = ctile_geo(F);
+    int tile;
+    const CGeo g = ctile_geo(F, k, tile);
     if (threadIdx.x == 0) {
         bar_init_expect(&bar, (uint32_t)(2 * S_V + SPY * SPX * 16));
         mg_tma4(sm, &mzt, &bar, g.c0, g.x0, g.y0, g.t);
@@ -437,7 +446,7 @@ __global__ void __launch_bounds__(256) k_mg_dir_tile(const __grid_constant__ CUt
         }
         f4st(p_out + (int64_t)i * k + col, pv);
     }
-    ctile_partials(run, k, g.c0, part);
+    ctile_partials(run, k, g.c0, tile, part);
 }
 
 // r -= alpha G p' with G p' from the staged p' tile; partials of r.D^-1 r; with XPAIR also
@@ -455,7 +464,8 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
     unsigned char *sm = mg_upd_raw + ((128u - (mg_saddr(mg_upd_raw) & 127u)) & 127u);
     const float *ps = reinterpret_cast<const float *>(sm);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + U_V);
-    const CGeo g = ctile_geo(F);
+    int tile;
+    const CGeo g = ctile_geo(F, k, tile);
     if (threadIdx.x == 0) {
         bar_init_expect(&bar, (uint32_t)(U_V + UPY * UPX * 16));
         mg_tma4(sm, &mpt, &bar, g.c0, g.x0 - 1, g.y0 - 1, g.t);
@@ -511,7 +521,7 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
         run[2] = fmaf(di * rv.z, rv.z, run[2]);
         run[3] = fmaf(di * rv.w, rv.w, run[3]);
     }
-    ctile_partials(run, k, g.c0, part);
+    ctile_partials(run, k, g.c0, tile, part);
 }
 
 // coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
