@@ -809,15 +809,26 @@ static er_status coarsen(const GridDev &f, cudaStream_t s, er_grid **out) {
                 if ((y & 1) && y + 1 < H && gyr[i] > 0.0)
                     gy[((size_t)t * (Hc - 1) + y / 2) * Wc + x / 2] += gyr[i];
             }
-    std::vector<er_tsv> tsv;
-    std::vector<er_pad> pads;
+    // TSV segments and pads that land on one aggregate act in parallel: their conductances are
+    // summed into one segment (one pad) per aggregate, so a coarse node has at most one TSV
+    // segment up and one down however many fine TSVs it gathers
+    const int64_t nc = (int64_t)T * Hc * Wc;
+    std::vector<double> tsum((size_t)nc, 0.0), psum((size_t)nc, 0.0);
     for (int64_t i = 0; i < n; ++i) {
         if (fl[i]) continue;
         const int x = (int)(i % W), y = (int)((i / W) % H), t = (int)(i / ((int64_t)W * H));
+        const int64_t J = ((int64_t)t * Hc + y / 2) * Wc + x / 2;
         for (int32_t e = tptr[i]; e < tptr[i + 1]; ++e)
-            if (tnbr[e] > i && tg[e] > 0.0) tsv.push_back({t, x / 2, y / 2, tg[e]});  // each segment once
+            if (tnbr[e] > i && tg[e] > 0.0) tsum[J] += tg[e];  // each segment once, from its lower end
         for (int32_t e = pptr[i]; e < pptr[i + 1]; ++e)
-            if (pg[e] > 0.0) pads.push_back({t, x / 2, y / 2, pg[e]});
+            if (pg[e] > 0.0) psum[J] += pg[e];
+    }
+    std::vector<er_tsv> tsv;
+    std::vector<er_pad> pads;
+    for (int64_t J = 0; J < nc; ++J) {
+        const int X = (int)(J % Wc), Y = (int)((J / Wc) % Hc), t = (int)(J / ((int64_t)Wc * Hc));
+        if (tsum[J] > 0.0) tsv.push_back({t, X, Y, tsum[J]});
+        if (psum[J] > 0.0) pads.push_back({t, X, Y, psum[J]});
     }
     std::vector<er_tier> tiers(T);
     for (int t = 0; t < T; ++t) {
