@@ -825,12 +825,14 @@ def run_ours(args, rank, world, local_rank):
                  (0, "k_mg_dir_tile", 3 * nk * es + coef),          # z, p in; p' out
                  (7, "k_mg_tile<true, true> (finest level)", int(2.25 * nk * es) + coef),
                  (6, "k_mg_tile<false, false> (finest level)", int(1.25 * nk * es) + coef),
-                 (5, "V-cycle on the coarse levels", int(3.5 * nk * es / 3))]
+                 (5, "V-cycle on the coarse levels", int(3.5 * nk * es / 3)),
+                 (2, "k_tma<MODE_R> (double-float residual)", 4 * nk * es + coef)]  # x {hi, lo}, b in; r out
     elif prec == "fp32":
         # (pass kind index, kernel, algorithmic bytes per launch)
         kinds = [(1, "k_tma<MODE_B>", 6 * nk * es + coef),   # odd iterations: r, p, x in; x, r, p' out
                  (4, "k_tma<MODE_B0>", 4 * nk * es + coef),  # even iterations: r, p in; r, p' out
-                 (0, "k_tma<MODE_A_DOT>", 2 * nk * es + coef)]  # r, p in
+                 (0, "k_tma<MODE_A_DOT>", 2 * nk * es + coef),  # r, p in
+                 (2, "k_tma<MODE_R> (double-float residual)", 4 * nk * es + coef)]  # x {hi, lo}, b in; r out
     else:
         kinds = [(0, "k_stencil<double,double,MODE_A_STORE>", 4 * nk * es + coef),
                  (1, "k_stream<double,MODE_S>", 6 * nk * es)]

@@ -83,7 +83,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
         total_ctas += til[c].n_ctas();
     }
     if (total_ctas >= INT32_MAX) return fail(ER_ERR_INVALID_ARG, "batch too large");
-    DevBuf b_b, b_c, b_r0, b_r1, b_p0, b_p1, b_x64, b_part, b_scal, b_int, b_cnt, b_items, b_work;
+    DevBuf b_b, b_c, b_r0, b_r1, b_p0, b_p1, b_xhl, b_part, b_scal, b_int, b_cnt, b_items, b_work;
     const size_t vbytes = nvec * 4;
     ER_CUDA(cudaMalloc(&b_b.p, vbytes));
     ER_CUDA(cudaMalloc(&b_c.p, vbytes));
@@ -91,7 +91,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
     ER_CUDA(cudaMalloc(&b_r1.p, vbytes));
     ER_CUDA(cudaMalloc(&b_p0.p, vbytes));
     ER_CUDA(cudaMalloc(&b_p1.p, vbytes));
-    ER_CUDA(cudaMalloc(&b_x64.p, vbytes * 2));
+    ER_CUDA(cudaMalloc(&b_xhl.p, vbytes * 2));
     ER_CUDA(cudaMalloc(&b_part.p, std::max<size_t>(npart, 1) * 8));
     ER_CUDA(cudaMalloc(&b_scal.p, (size_t)n * 6 * k * 8));
     ER_CUDA(cudaMalloc(&b_int.p, nint * 4));
@@ -112,12 +112,12 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
         it.p[0] = fvec(b_p0, c); it.p[1] = fvec(b_p1, c);
         it.c = fvec(b_c, c);
         it.b = fvec(b_b, c);
-        it.x64 = reinterpret_cast<double *>(b_x64.p) + off_vec[c];
+        it.xhl = reinterpret_cast<float2 *>(b_xhl.p) + off_vec[c];
         er_status st = ER_OK;
-        const void *bases[8] = {it.r[0], it.r[1], it.p[0], it.p[1], it.c, it.x64, it.b, g.coef32};
+        const void *bases[8] = {it.r[0], it.r[1], it.p[0], it.p[1], it.c, it.xhl, it.b, g.coef32};
         for (int m = 0; m < 8 && st == ER_OK; ++m)
             st = m == 7 ? fp32_make_map(&it.tm[m], false, bases[m], 4, 4, g)
-                        : fp32_make_map(&it.tm[m], m == 5, bases[m], k, 32, g);
+                        : fp32_make_map(&it.tm[m], m == 5, bases[m], k, 32, g);  // xhl: 8-byte pairs
         if (st != ER_OK) return st;
         KArgs<float, float> &a = it.a;
         a.T_ = g.T; a.W = g.W; a.H = g.H; a.k = k;

@@ -15,11 +15,11 @@ enum Mode {
     MODE_A_DOT = 0,    // p' = z + beta p, q = G p', dot p'.q (no stores)
     MODE_A_STORE = 1,  // as A, storing p' and q
     MODE_B = 2,        // recompute p', q; x += alpha p'; r -= alpha q; store x, r, p'; dot r.z
-    MODE_R = 3,        // FP64 residual r = b - G x; dot r.z
+    MODE_R = 3,        // residual r = b - G x (FP64 form; double-float in the FP32 form); dot r.z
     MODE_S = 4,        // streaming x += alpha p', r -= alpha q; dot r.r
     MODE_INIT = 5,     // r = b (scaled in the FP64 form), x = 0, p = 0; dot r.z
     MODE_UNSCALE = 6,  // final Z from the iterate
-    MODE_ACCUM = 7,    // FP32 form: x64 += x, x = 0
+    MODE_ACCUM = 7,    // FP32 form: xhl += x, x = 0
     MODE_B0 = 8        // FP32 form, even iterations: as B without touching x (x is updated
                        // with two iterations' steps in the following odd one)
 };
@@ -32,7 +32,7 @@ struct KArgs {
     int tiles_x, tiles_y, rows, n_spatial, n_colblk, cb_fast;
     const T *r_in, *p_in, *b_in, *q_in;
     T *x, *r_out, *p_out, *q_out;
-    double *x64;                        // FP32 form: FP64 iterate
+    float2 *xhl;                        // FP32 form: iterate as double-float pairs {hi, lo}
     const C *cE, *cS, *tsv_c;           // FP64 form: couplings of D^-1/2 G D^-1/2
     const float4 *coef;                 // FP32 form: per node {1/d, gE, gS, pad}
     const float *tsv_g32;               // FP32 form: TSV conductance per CSR entry
@@ -161,16 +161,15 @@ __device__ inline void finalize_column(const KArgs<T, C> &a, int j, double total
     nact += a.active[j];
 }
 
-// sred holds kNX * KB per-thread partials on entry (and at least (kThreads / KB) * KB
-// doubles of room).  Writes this CTA's column partials, and the last CTA of the column
-// block folds all spatial partials in tile order into the per-column scalars.
+// Threads < KB hold this CTA's partial s of column cb * KB + threadIdx.x.  Writes the CTA's
+// column partials, and the last CTA of the column block folds all spatial partials in tile
+// order into the per-column scalars; sred is scratch of at least (kThreads / KB) * KB
+// doubles, free on entry (reads of it by threads < KB must precede the call).
 template <typename T, typename C, int MODE, int KB>
-__device__ inline void reduce_and_finalize(const KArgs<T, C> &a, double *sred, int spatial, int cb) {
+__device__ inline void write_and_finalize(const KArgs<T, C> &a, double *sred, double s, int spatial, int cb) {
     __shared__ bool s_last;
     __shared__ int s_nact;
     if (threadIdx.x < KB) {
-        double s = 0.0;
-        for (int xx = 0; xx < kNX; ++xx) s += sred[xx * KB + threadIdx.x];
         const int j = cb * KB + threadIdx.x;
         if (j < a.k) a.part[(int64_t)spatial * a.k + j] = s;
     }
@@ -187,10 +186,10 @@ __device__ inline void reduce_and_finalize(const KArgs<T, C> &a, double *sred, i
     constexpr int G = kThreads / KB;
     const int cj = threadIdx.x % KB, gl = threadIdx.x / KB;
     const int j = cb * KB + cj;
-    double s = 0.0;
+    double acc = 0.0;
     if (j < a.k)
-        for (int t = gl; t < a.n_spatial; t += G) s += __ldcg(&a.part[(int64_t)t * a.k + j]);
-    sred[gl * KB + cj] = s;
+        for (int t = gl; t < a.n_spatial; t += G) acc += __ldcg(&a.part[(int64_t)t * a.k + j]);
+    sred[gl * KB + cj] = acc;
     __syncthreads();
     if (threadIdx.x < KB && j < a.k) {
         double tot = 0.0;
@@ -204,6 +203,17 @@ __device__ inline void reduce_and_finalize(const KArgs<T, C> &a, double *sred, i
         if (MODE != MODE_A_DOT && MODE != MODE_A_STORE) a.col_active[cb] = s_nact;
         a.counter[cb] = 0u;
     }
+}
+
+// sred holds kNX * KB per-thread partials on entry (and at least (kThreads / KB) * KB
+// doubles of room): sums them per column and calls write_and_finalize.
+template <typename T, typename C, int MODE, int KB>
+__device__ inline void reduce_and_finalize(const KArgs<T, C> &a, double *sred, int spatial, int cb) {
+    double s = 0.0;
+    if (threadIdx.x < KB)
+        for (int xx = 0; xx < kNX; ++xx) s += sred[xx * KB + threadIdx.x];
+    __syncthreads();
+    write_and_finalize<T, C, MODE, KB>(a, sred, s, spatial, cb);
 }
 
 // Block index -> (tile x, tile y, tier, column block).  With cb_fast the column blocks
@@ -232,7 +242,7 @@ struct Workspace {
     er_precision prec = ER_FP64;
     Tiling til;
     void *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr}, *q = nullptr;
-    double *x64 = nullptr;                    // FP32 form: FP64 iterate
+    float2 *xhl = nullptr;                    // FP32 form: iterate as double-float pairs {hi, lo}
     double *part = nullptr, *scal = nullptr;  // scal: alpha, beta, rho, rho0, resid, alpha_prev (k each)
     int *ints = nullptr;                      // active[k], col_active[n_colblk], err
     unsigned *counter = nullptr;
@@ -247,7 +257,7 @@ struct Workspace {
     double g_tol = -1.0;
     int g_iters = 0, g_parity = -1;
     // FP32 form: TMA descriptors of the workspace vectors and of the caller's arrays
-    CUtensorMap tm_r[2], tm_p[2], tm_x64, tm_coef, tm_c, tm_b;
+    CUtensorMap tm_r[2], tm_p[2], tm_xhl, tm_coef, tm_c, tm_b;
     const void *tm_c_ptr = nullptr, *tm_b_ptr = nullptr;
 };
 
@@ -280,13 +290,13 @@ void prof_begin(Workspace &w, Prof *pf, int kind);
 void prof_end(Workspace &w, Prof *pf, int kind);
 void flush_prof(Workspace &w, Prof &pf);  // after a synchronisation of w.s
 
-// One network of a batch: its tensor maps (r0, r1, p0, p1, x, x64, b, coef), its kernel
+// One network of a batch: its tensor maps (r0, r1, p0, p1, x, xhl, b, coef), its kernel
 // arguments (geometry, coefficients, scalars, partials) and its vectors.
 struct BatchItem {
     CUtensorMap tm[8];
     KArgs<float, float> a;
     float *r[2], *p[2], *c;
-    double *x64;
+    float2 *xhl;
     const float *b;
 };
 

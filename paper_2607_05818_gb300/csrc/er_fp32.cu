@@ -2,20 +2,27 @@
 //
 // The FP32 iterations apply the network operator in edge-difference form,
 //   (G v)_i = pad_i v_i + sum_{j ~ i} g_ij (v_i - v_j),
-// with every conductance rounded to FP32 once at grid creation.  The FP64 residual
-// b - G x uses exactly the same FP32 conductances (promoted), so the FP32 recursion and
-// the FP64 residual see one operator, and the Laplacian structure (zero row sums apart
-// from the pads) is exact.  Rounding each conductance by at most a relative u = 2^-24
-// keeps every effective resistance within [R/(1+u), R/(1-u)] (Rayleigh monotonicity:
-// the perturbed network lies between the original scaled by 1-u and by 1+u).
+// with every conductance rounded to FP32 once at grid creation.  The accurate residual
+// b - G x uses exactly the same FP32 conductances, so the FP32 recursion and the accurate
+// residual see one operator, and the Laplacian structure (zero row sums apart from the
+// pads) is exact.  Rounding each conductance by at most a relative u = 2^-24 keeps every
+// effective resistance within [R/(1+u), R/(1-u)] (Rayleigh monotonicity: the perturbed
+// network lies between the original scaled by 1-u and by 1+u).
+//
+// The accurate iterate and residual are double-float: a value is the unevaluated sum
+// hi + lo of two FP32 numbers (about 48 significant bits), and the residual is formed with
+// error-free transformations (TwoSum, FMA TwoProduct) on the FP32 pipes.  FP64 arithmetic
+// runs at 1/64 of the FP32 rate on this GPU, so an FP64 residual pass was bound by the
+// FP64 units, not by memory; the double-float pass moves the same bytes (8 per iterate
+// entry) and is bandwidth-bound.
 //
 // Jacobi preconditioning: z = D^-1 r with D = diag(G) from the same conductances.
 // Passes per iteration (vectors [n][k] FP32, k innermost):
 //   A  p' = z + beta p; q = G p'; dot p'.q                          reads r, p
 //   B  recompute p', q; x += alpha p'; r' = r - alpha q; dot r'.z'  reads r, p, x;
 //                                                                  writes x, r', p'
-// Every `replace_every` iterations the correction x is folded into an FP64 iterate
-// (x64 += x, x = 0) and the FP64 residual r = b - G x64 replaces the recursive one
+// Every `replace_every` iterations the correction x is folded into the double-float iterate
+// (xhl += x, x = 0) and the accurate residual r = b - G xhl replaces the recursive one
 // (a reliable update: CG continues with the same search direction).
 //
 // Staging: a CTA owns 30 nodes along x (one halo node each side) and a run of y rows of
@@ -97,11 +104,11 @@ struct Layout<MODE_B0> {  // even iterations; stage: r, p, coef
     static constexpr int NS = 4, OFF_R = 0, OFF_P = 4096, OFF_X = -1, OFF_COEF = 8192, BYTES = 8704;
 };
 template <>
-struct Layout<MODE_R> {  // stage: x64 (FP64), b, coef
+struct Layout<MODE_R> {  // stage: xhl (8-byte {hi, lo} pairs), b, coef
     static constexpr int NS = 4, OFF_R = 8192, OFF_P = -1, OFF_X = 0, OFF_COEF = 12288, BYTES = 12800;
 };
 // dynamic shared memory: NS stages, then a two-row ring of the per-node operand
-// (p' in FP32, x64 in FP64), plus slack for 128-byte alignment
+// (p' in FP32, xhl as {hi, lo} pairs), plus slack for 128-byte alignment
 template <int MODE>
 constexpr int ring_bytes() { return MODE == MODE_R ? 2 * kNX * 256 : 2 * kNX * 128; }
 template <int MODE>
@@ -112,9 +119,49 @@ __device__ __forceinline__ float4 lds4(const unsigned char *p) { return *reinter
 // component v of a float4 (v is a compile-time constant after unrolling)
 __device__ __forceinline__ float f4(const float4 &f, int v) { return v == 0 ? f.x : v == 1 ? f.y : v == 2 ? f.z : f.w; }
 
+// Double-float arithmetic of the iterate and the residual.  Error-free transformations:
+// TwoSum (Knuth; s + e = a + b exactly) and the FMA TwoProduct (p + e = a * b exactly),
+// as in Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26
+// (2005).  The _rn intrinsics are never contracted into FMAs, which would corrupt the
+// error terms.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// {hi, lo} + c, renormalised (hi = the sum rounded to FP32, lo = the rest)
+__device__ __forceinline__ float2 df_add(float2 X, float c) {
+    const float2 t = two_sum(X.x, c);
+    return two_sum(t.x, __fadd_rn(t.y, X.y));
+}
+
+// q = pad X_i + sum_j g_ij (X_i - X_j) for FP32 conductances and double-float X, held as
+// the unevaluated sum S + C (C collects every rounding error of the terms and of S)
+struct DfSum {
+    float S, C;
+    __device__ __forceinline__ void init_prod(float g, float2 X) {  // S + C = g X
+        S = __fmul_rn(g, X.x);
+        C = fmaf(g, X.y, fmaf(g, X.x, -S));
+    }
+    __device__ __forceinline__ void add_edge(float g, float2 Xi, float2 Xj) {  // S + C += g (Xi - Xj)
+        const float2 d = two_sum(Xi.x, -Xj.x);
+        const float dl = __fadd_rn(d.y, __fsub_rn(Xi.y, Xj.y));
+        const float p = __fmul_rn(g, d.x);
+        const float pe = fmaf(g, dl, fmaf(g, d.x, -p));
+        const float2 t = two_sum(S, p);
+        S = t.x;
+        C = __fadd_rn(C, __fadd_rn(t.y, pe));
+    }
+    __device__ __forceinline__ float residual(float b) const {  // b - (S + C), rounded once
+        const float2 t = two_sum(b, -S);
+        return __fadd_rn(t.x, __fsub_rn(t.y, C));
+    }
+};
+
 // One pass over a CTA's tile.  Step ri (row y = y0 - 1 + ri) waits for its stage, reads the
-// thread's own node from it into registers (r, p or x64, x, coefficients), forms the
-// operand v = p' (or x64) and, for row y - 1, finishes q = G v from registers (north,
+// thread's own node from it into registers (r, p or xhl, x, coefficients), forms the
+// operand v = p' (or xhl) and, for row y - 1, finishes q = G v from registers (north,
 // centre, south) and the ring (x-neighbours of the centre row); then it publishes v in the
 // ring, synchronises once, and the stage is refilled NS rows ahead.
 template <int MODE>
@@ -124,7 +171,7 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
     using L = Layout<MODE>;
     constexpr int V = 4, KB = kTPN * V;  // 32 columns per CTA
     constexpr bool R64 = MODE == MODE_R;
-    using Cv = typename std::conditional<R64, double, float>::type;  // operand type
+    using Cv = typename std::conditional<R64, float2, float>::type;  // operand type ({hi, lo} in MODE_R)
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     Cv *ring = reinterpret_cast<Cv *>(smem + L::NS * L::BYTES);  // [2][kNX][KB]
     __shared__ __align__(8) uint64_t bars[L::NS];
@@ -164,7 +211,7 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
         const int y = y0 - 1 + ri;
         mbar_arrive_expect_tx(&bars[s], L::BYTES);
         if constexpr (R64) {
-            tma_load4(st + L::OFF_X, tm0, &bars[s], c0, xb, y, t);  // x64
+            tma_load4(st + L::OFF_X, tm0, &bars[s], c0, xb, y, t);  // xhl
             tma_load4(st + L::OFF_R, tm1, &bars[s], c0, xb, y, t);  // b
         } else {
             tma_load4(st + L::OFF_R, tm0, &bars[s], c0, xb, y, t);
@@ -203,10 +250,12 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
     float4 cfc = make_float4(0.f, 0.f, 0.f, 0.f);  // {+-1/d, gE, gS, pad} of row y-1, own node
     float gwc = 0.f, gsn = 0.f;                    // gE of the west node (row y-1); gS of row y-2
     float run[V] = {0.f, 0.f, 0.f, 0.f};
-    double acc[V] = {0.0, 0.0, 0.0, 0.0};
+    float2 acc[V];  // double-float per-column sums of the FP32 runs (no FP64 arithmetic per node)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = make_float2(0.f, 0.f);
     int nrun = 0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) vn[v] = vc[v] = (Cv)0, rc[v] = 0.f;
+    for (int v = 0; v < V; ++v) vn[v] = vc[v] = Cv{}, rc[v] = 0.f;
 
 #pragma unroll 2
     for (int ri = 0; ri < nrow; ++ri) {
@@ -218,9 +267,10 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
         const float4 cfs = lds4(st + L::OFF_COEF + xl * 16);
         const float gws = xl > 0 ? lds4(st + L::OFF_COEF + (xl - 1) * 16).y : 0.f;
         if constexpr (R64) {
-            const double2 lo = *reinterpret_cast<const double2 *>(st + L::OFF_X + xl * 256 + lc * 32);
-            const double2 hi = *reinterpret_cast<const double2 *>(st + L::OFF_X + xl * 256 + lc * 32 + 16);
-            vs[0] = lo.x; vs[1] = lo.y; vs[2] = hi.x; vs[3] = hi.y;
+            const float4 c01 = lds4(st + L::OFF_X + xl * 256 + lc * 32);
+            const float4 c23 = lds4(st + L::OFF_X + xl * 256 + lc * 32 + 16);
+            vs[0] = make_float2(c01.x, c01.y); vs[1] = make_float2(c01.z, c01.w);
+            vs[2] = make_float2(c23.x, c23.y); vs[3] = make_float2(c23.z, c23.w);
             const float4 b = lds4(st + L::OFF_R + xl * 128 + lc * 16);
             rs[0] = b.x; rs[1] = b.y; rs[2] = b.z; rs[3] = b.w;
         } else {
@@ -261,19 +311,22 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
             const int64_t i = tbase + (int64_t)y * a.W + x;
             const int64_t idx = i * a.k + col;
             const Cv *rw = ring + ((ri - 1) & 1) * kNX * KB;
-            Cv vw[V], ve[V], q[V];
+            Cv vw[V], ve[V];
+            float q[V];
             if constexpr (R64) {
-                const double2 *pw = reinterpret_cast<const double2 *>(rw + (xl - 1) * KB + lc * V);
-                const double2 *pe = reinterpret_cast<const double2 *>(rw + (xl + 1) * KB + lc * V);
-                vw[0] = pw[0].x; vw[1] = pw[0].y; vw[2] = pw[1].x; vw[3] = pw[1].y;
-                ve[0] = pe[0].x; ve[1] = pe[0].y; ve[2] = pe[1].x; ve[3] = pe[1].y;
+                const float4 *pw = reinterpret_cast<const float4 *>(rw + (xl - 1) * KB + lc * V);
+                const float4 *pe = reinterpret_cast<const float4 *>(rw + (xl + 1) * KB + lc * V);
+                vw[0] = make_float2(pw[0].x, pw[0].y); vw[1] = make_float2(pw[0].z, pw[0].w);
+                vw[2] = make_float2(pw[1].x, pw[1].y); vw[3] = make_float2(pw[1].z, pw[1].w);
+                ve[0] = make_float2(pe[0].x, pe[0].y); ve[1] = make_float2(pe[0].z, pe[0].w);
+                ve[2] = make_float2(pe[1].x, pe[1].y); ve[3] = make_float2(pe[1].z, pe[1].w);
             } else {
                 const float4 w4 = *reinterpret_cast<const float4 *>(rw + (xl - 1) * KB + lc * V);
                 const float4 e4 = *reinterpret_cast<const float4 *>(rw + (xl + 1) * KB + lc * V);
                 vw[0] = w4.x; vw[1] = w4.y; vw[2] = w4.z; vw[3] = w4.w;
                 ve[0] = e4.x; ve[1] = e4.y; ve[2] = e4.z; ve[3] = e4.w;
             }
-            const Cv gp = cfc.w, ge = cfc.y, gs = cfc.z, gw = gwc, gn = gsn;
+            const float gp = cfc.w, ge = cfc.y, gs = cfc.z, gw = gwc, gn = gsn;
             if constexpr (MODE == MODE_A_DOT) {
                 // p'.Gp' as a sum over edges: pad p^2 + gE (p - pE)^2 + gS (p - pS)^2 at each node,
                 // plus half of every TSV segment at each of its two ends
@@ -286,32 +339,32 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
                     q[v] = e;
                 }
             } else if constexpr (R64) {
-                // diagonal form: d v - sum_j g_j v_j, d summed exactly in FP64 from the FP32 g's
-                Cv d = gp + ge + gw + gs + gn;
+                // edge-difference form in double-float: q = pad X_i + sum_j g_ij (X_i - X_j),
+                // held as the unevaluated sum S + C
+                DfSum acc4[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    Cv qq = -ge * ve[v];
-                    qq = fma(-gw, vw[v], qq);
-                    qq = fma(-gs, vs[v], qq);
-                    qq = fma(-gn, vn[v], qq);
-                    q[v] = qq;
+                    acc4[v].init_prod(gp, vc[v]);
+                    acc4[v].add_edge(ge, vc[v], ve[v]);
+                    acc4[v].add_edge(gw, vc[v], vw[v]);
+                    acc4[v].add_edge(gs, vc[v], vs[v]);
+                    acc4[v].add_edge(gn, vc[v], vn[v]);
                 }
                 if (cfc.x < 0.f) {
                     const int e1 = a.tsv_ptr[i + 1];
                     for (int e = a.tsv_ptr[i]; e < e1; ++e) {
                         const int64_t jdx = (int64_t)a.tsv_nbr[e] * a.k + col;
-                        const double g = a.tsv_g32[e];
-                        const double2 lo = *reinterpret_cast<const double2 *>(a.x64 + jdx);
-                        const double2 hi = *reinterpret_cast<const double2 *>(a.x64 + jdx + 2);
-                        d += g;
-                        q[0] = fma(-g, lo.x, q[0]);
-                        q[1] = fma(-g, lo.y, q[1]);
-                        q[2] = fma(-g, hi.x, q[2]);
-                        q[3] = fma(-g, hi.y, q[3]);
+                        const float g = a.tsv_g32[e];
+                        const float4 c01 = *reinterpret_cast<const float4 *>(a.xhl + jdx);
+                        const float4 c23 = *reinterpret_cast<const float4 *>(a.xhl + jdx + 2);
+                        acc4[0].add_edge(g, vc[0], make_float2(c01.x, c01.y));
+                        acc4[1].add_edge(g, vc[1], make_float2(c01.z, c01.w));
+                        acc4[2].add_edge(g, vc[2], make_float2(c23.x, c23.y));
+                        acc4[3].add_edge(g, vc[3], make_float2(c23.z, c23.w));
                     }
                 }
 #pragma unroll
-                for (int v = 0; v < V; ++v) q[v] = fma(d, vc[v], q[v]);
+                for (int v = 0; v < V; ++v) q[v] = acc4[v].residual(rc[v]);  // b - q, rounded once
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -323,7 +376,7 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
                     q[v] = qq;
                 }
             }
-            if (!R64 && cfc.x < 0.f) {  // node with TSV segments (FP32 passes)
+            if constexpr (!R64) if (cfc.x < 0.f) {  // node with TSV segments (FP32 passes)
                 const int e1 = a.tsv_ptr[i + 1];
                 for (int e = a.tsv_ptr[i]; e < e1; ++e) {
                     const int j = a.tsv_nbr[e];
@@ -346,7 +399,7 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
                 float ro[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    ro[v] = (float)((double)rc[v] - q[v]);
+                    ro[v] = q[v];
                     run[v] = fmaf(dinv * ro[v], ro[v], run[v]);
                 }
                 stv<float, float, V>(a.r_out + idx, ro);
@@ -368,7 +421,7 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
                 if (++nrun == 8) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        acc[v] += (double)run[v];
+                        acc[v] = df_add(acc[v], run[v]);
                         run[v] = 0.f;
                     }
                     nrun = 0;
@@ -379,8 +432,8 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
         {
             Cv *wr = ring + (ri & 1) * kNX * KB + xl * KB + lc * V;
             if constexpr (R64) {
-                reinterpret_cast<double2 *>(wr)[0] = make_double2(vs[0], vs[1]);
-                reinterpret_cast<double2 *>(wr)[1] = make_double2(vs[2], vs[3]);
+                reinterpret_cast<float4 *>(wr)[0] = make_float4(vs[0].x, vs[0].y, vs[1].x, vs[1].y);
+                reinterpret_cast<float4 *>(wr)[1] = make_float4(vs[2].x, vs[2].y, vs[3].x, vs[3].y);
             } else {
                 *reinterpret_cast<float4 *>(wr) = make_float4(vs[0], vs[1], vs[2], vs[3]);
             }
@@ -409,11 +462,23 @@ __device__ __forceinline__ void tma_pass(const KArgs<float, float> &a, const CUt
         }
     }
     __syncthreads();
-    double *sred = reinterpret_cast<double *>(smem);  // the stage ring is free now
+    // per column: the kNX node slots of the CTA summed in a fixed order, in double-float
+    float2 *sdf = reinterpret_cast<float2 *>(smem);  // the stage ring is free now
 #pragma unroll
-    for (int v = 0; v < V; ++v) sred[xl * KB + lc * V + v] = own ? acc[v] + (double)run[v] : 0.0;
+    for (int v = 0; v < V; ++v) sdf[xl * KB + lc * V + v] = own ? df_add(acc[v], run[v]) : make_float2(0.f, 0.f);
     __syncthreads();
-    reduce_and_finalize<float, float, MODE, KB>(a, sred, spatial, cb);
+    double s_col = 0.0;
+    if (threadIdx.x < KB) {
+        float2 t = sdf[threadIdx.x];
+        for (int xx = 1; xx < kNX; ++xx) {
+            const float2 u = sdf[xx * KB + threadIdx.x];
+            const float2 h = two_sum(t.x, u.x);
+            t = two_sum(h.x, __fadd_rn(h.y, __fadd_rn(t.y, u.y)));
+        }
+        s_col = (double)t.x + (double)t.y;
+    }
+    __syncthreads();
+    write_and_finalize<float, float, MODE, KB>(a, reinterpret_cast<double *>(smem), s_col, spatial, cb);
 }
 
 template <int MODE>
@@ -443,7 +508,7 @@ __device__ __forceinline__ void fp32_stream_pass(const KArgs<float, float> &a, i
         for (int y = y0; y < y1; ++y) {
             const int64_t i = tbase + (int64_t)y * a.W + x;
             const int64_t idx = i * a.k + col;
-            if constexpr (MODE == MODE_INIT) {  // r = b, x = 0, p = 0, x64 = 0; dot b.D^-1 b
+            if constexpr (MODE == MODE_INIT) {  // r = b, x = 0, p = 0, xhl = 0; dot b.D^-1 b
                 float b[V];
                 const float z[V] = {0.f, 0.f, 0.f, 0.f};
                 ldv<float, float, V>(a.b_in + idx, b);
@@ -451,24 +516,28 @@ __device__ __forceinline__ void fp32_stream_pass(const KArgs<float, float> &a, i
                 stv<float, float, V>(a.r_out + idx, b);
                 stv<float, float, V>(a.x + idx, z);
                 stv<float, float, V>(a.p_out + idx, z);
-                *reinterpret_cast<double2 *>(a.x64 + idx) = make_double2(0.0, 0.0);
-                *reinterpret_cast<double2 *>(a.x64 + idx + 2) = make_double2(0.0, 0.0);
+                *reinterpret_cast<float4 *>(a.xhl + idx) = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4 *>(a.xhl + idx + 2) = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v].add(dinv * b[v], b[v]);
-            } else if constexpr (MODE == MODE_ACCUM) {  // x64 += x; x = 0
+            } else if constexpr (MODE == MODE_ACCUM) {  // xhl += x (double-float); x = 0
                 float c[V];
                 const float z[V] = {0.f, 0.f, 0.f, 0.f};
                 ldv<float, float, V>(a.x + idx, c);
-                double2 lo = *reinterpret_cast<const double2 *>(a.x64 + idx);
-                double2 hi = *reinterpret_cast<const double2 *>(a.x64 + idx + 2);
-                lo.x += (double)c[0]; lo.y += (double)c[1]; hi.x += (double)c[2]; hi.y += (double)c[3];
-                *reinterpret_cast<double2 *>(a.x64 + idx) = lo;
-                *reinterpret_cast<double2 *>(a.x64 + idx + 2) = hi;
+                float4 *xp = reinterpret_cast<float4 *>(a.xhl + idx);
+                const float4 c01 = xp[0], c23 = xp[1];
+                const float2 x0 = df_add(make_float2(c01.x, c01.y), c[0]);
+                const float2 x1 = df_add(make_float2(c01.z, c01.w), c[1]);
+                const float2 x2 = df_add(make_float2(c23.x, c23.y), c[2]);
+                const float2 x3 = df_add(make_float2(c23.z, c23.w), c[3]);
+                xp[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                xp[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
                 stv<float, float, V>(a.x + idx, z);
-            } else {  // MODE_UNSCALE: Z = x64 rounded to FP32
-                const double2 lo = *reinterpret_cast<const double2 *>(a.x64 + idx);
-                const double2 hi = *reinterpret_cast<const double2 *>(a.x64 + idx + 2);
-                const float o[V] = {(float)lo.x, (float)lo.y, (float)hi.x, (float)hi.y};
+            } else {  // MODE_UNSCALE: Z = hi + lo rounded to FP32
+                const float4 *xp = reinterpret_cast<const float4 *>(a.xhl + idx);
+                const float4 c01 = xp[0], c23 = xp[1];
+                const float o[V] = {__fadd_rn(c01.x, c01.y), __fadd_rn(c01.z, c01.w), __fadd_rn(c23.x, c23.y),
+                                    __fadd_rn(c23.z, c23.w)};
                 stv<float, float, V>(a.x + idx, o);
             }
         }
@@ -496,12 +565,12 @@ __device__ __forceinline__ void batch_args(const BatchItem &it, int cur, int rmo
     a = it.a;
     a.rmode = rmode;
     if constexpr (MODE == MODE_R) {
-        a.x64 = it.x64;
+        a.xhl = it.xhl;
         a.r_out = it.r[cur];
     } else if constexpr (MODE == MODE_INIT) {
-        a.b_in = it.b; a.r_out = it.r[0]; a.x = it.c; a.p_out = it.p[0]; a.x64 = it.x64;
+        a.b_in = it.b; a.r_out = it.r[0]; a.x = it.c; a.p_out = it.p[0]; a.xhl = it.xhl;
     } else if constexpr (MODE == MODE_ACCUM || MODE == MODE_UNSCALE) {
-        a.x = it.c; a.x64 = it.x64;
+        a.x = it.c; a.xhl = it.xhl;
     } else {
         a.r_in = it.r[cur]; a.p_in = it.p[cur]; a.x = it.c;
         a.r_out = it.r[1 - cur]; a.p_out = it.p[1 - cur];
@@ -609,7 +678,7 @@ er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z) 
             if (s == ER_OK) s = make_map(&w.tm_p[i], F32, 4, w.p[i], w.k, 32, g);
             if (s != ER_OK) return s;
         }
-        er_status s = make_map(&w.tm_x64, F64, 8, w.x64, w.k, 32, g);
+        er_status s = make_map(&w.tm_xhl, F64, 8, w.xhl, w.k, 32, g);  // 8-byte {hi, lo} pairs, copied as bytes
         if (s == ER_OK) s = make_map(&w.tm_coef, F32, 4, g.coef32, 4, 4, g);
         if (s != ER_OK) return s;
     }
@@ -657,7 +726,7 @@ void fp32_init(const GridDev &g, Workspace &w, const void *Yt, void *Z, double t
     a.r_out = (float *)w.r[0];
     a.x = (float *)Z;
     a.p_out = (float *)w.p[0];
-    a.x64 = w.x64;
+    a.xhl = w.xhl;
     launch_stream<MODE_INIT>(a, w, pf, ER_PASS_OTHER);
 }
 
@@ -687,7 +756,7 @@ int fp32_iterate(const GridDev &g, Workspace &w, void *Z, double tol, int cur, P
 void fp32_accum(const GridDev &g, Workspace &w, void *Z, Prof *pf) {
     auto a = base_args<float, float>(g, w, 0.0);
     a.x = (float *)Z;
-    a.x64 = w.x64;
+    a.xhl = w.xhl;
     launch_stream<MODE_ACCUM>(a, w, pf, ER_PASS_OTHER);
 }
 
@@ -695,10 +764,10 @@ void fp32_residual(const GridDev &g, Workspace &w, const void *Yt, double tol, i
     TArgs ta;
     std::memset(&ta, 0, sizeof(ta));
     ta.a = base_args<float, float>(g, w, tol);
-    ta.a.x64 = w.x64;
+    ta.a.xhl = w.xhl;
     ta.a.r_out = (float *)w.r[cur_buf];
     ta.a.rmode = rmode;
-    ta.tm[0] = w.tm_x64;
+    ta.tm[0] = w.tm_xhl;
     ta.tm[1] = w.tm_b;
     ta.tm[3] = w.tm_coef;
     (void)Yt;
@@ -708,7 +777,7 @@ void fp32_residual(const GridDev &g, Workspace &w, const void *Yt, double tol, i
 void fp32_final(const GridDev &g, Workspace &w, void *Z, Prof *pf) {
     auto a = base_args<float, float>(g, w, 0.0);
     a.x = (float *)Z;
-    a.x64 = w.x64;
+    a.xhl = w.xhl;
     launch_stream<MODE_UNSCALE>(a, w, pf, ER_PASS_OTHER);
 }
 

@@ -64,6 +64,7 @@ struct SketchView {
     const int32_t *pad_ptr;
     const int64_t *pad_eid;
     const double *pad_g;
+    const float2 *sq_x, *sq_y, *sq_tsv, *sq_pad;
     const uint8_t *floating;
 };
 
@@ -125,6 +126,78 @@ __global__ void __launch_bounds__(256) k_sketch(SketchView g, int k, uint64_t ke
         reinterpret_cast<float4 *>(out)[0] =
             make_float4((float)acc[0], (float)acc[1], (float)acc[2], (float)acc[3]);
     }
+}
+
+// FP32 sketch, the same sums without FP64 arithmetic (FP64 runs at 1/64 of the FP32 rate
+// on this GPU, and the FP64 kernel above is bound by it).  Each term sqrt(w_e)/sqrt(k) is
+// the double-float product of the stored {hi, lo} square root and {hi, lo} of 1/sqrt(k);
+// the terms are summed per column as S + C with TwoSum (Knuth) and rounded once, so the
+// output is the FP32 rounding of the sum to within rare one-ulp ties.  The sign is the top
+// bit of SplitMix64; its last xor-shift leaves bit 63 unchanged and is skipped.
+__device__ __forceinline__ uint32_t sketch_sign(uint64_t key, uint64_t hi, uint32_t j) {
+    uint64_t z = (key ^ (hi | j)) + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return (uint32_t)(z >> 63);
+}
+
+struct SketchAcc32 {
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+    // += sigma sqrt(w) rk sign(e, j0 + v); sq = sqrt(w) as {hi, lo}, rk = 1/sqrt(k) as {hi, lo}
+    __device__ __forceinline__ void term(uint64_t key, int64_t e, int j0, float2 sq, float2 rk, bool neg) {
+        const float p0 = __fmul_rn(sq.x, rk.x);
+        const float e0 = fmaf(sq.y, rk.x, fmaf(sq.x, rk.y, fmaf(sq.x, rk.x, -p0)));
+        const float p = neg ? -p0 : p0, pe = neg ? -e0 : e0;
+        const uint64_t hi = (uint64_t)e << 32;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const bool m = sketch_sign(key, hi, (uint32_t)(j0 + v)) != 0;
+            const float a = m ? -p : p, ae = m ? -pe : pe;
+            const float t = __fadd_rn(S[v], a);
+            const float bb = __fsub_rn(t, S[v]);
+            const float err = __fadd_rn(__fsub_rn(S[v], __fsub_rn(t, bb)), __fsub_rn(a, bb));
+            S[v] = t;
+            C[v] = __fadd_rn(C[v], __fadd_rn(err, ae));
+        }
+    }
+};
+
+__global__ void __launch_bounds__(256) k_sketch32(SketchView g, int k, uint64_t key, float2 rk, float *Yt) {
+    const int64_t nq = k / 4;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= g.n * nq) return;
+    const int64_t i = tid / nq;
+    const int j0 = (int)(tid - i * nq) * 4;
+    SketchAcc32 acc;
+    if (!g.floating[i]) {
+        const int x = (int)(i % g.W);
+        const int64_t ty = i / g.W;
+        const int y = (int)(ty % g.H);
+        const int t = (int)(ty / g.H);
+        // an absent segment has w = 0, so sqrt(w).hi = 0 (tested in FP32: no FP64 compare)
+        if (x > 0) {  // x-segment (x-1, y)-(x, y): this node is the higher end
+            const float2 q = g.sq_x[i - 1];
+            if (q.x > 0.f) acc.term(key, ((int64_t)t * g.H + y) * (g.W - 1) + x - 1, j0, q, rk, true);
+        }
+        if (x < g.W - 1) {
+            const float2 q = g.sq_x[i];
+            if (q.x > 0.f) acc.term(key, ((int64_t)t * g.H + y) * (g.W - 1) + x, j0, q, rk, false);
+        }
+        if (y > 0) {
+            const float2 q = g.sq_y[i - g.W];
+            if (q.x > 0.f) acc.term(key, g.ex_slots + ((int64_t)t * (g.H - 1) + y - 1) * g.W + x, j0, q, rk, true);
+        }
+        if (y < g.H - 1) {
+            const float2 q = g.sq_y[i];
+            if (q.x > 0.f) acc.term(key, g.ex_slots + ((int64_t)t * (g.H - 1) + y) * g.W + x, j0, q, rk, false);
+        }
+        for (int e = g.tsv_ptr[i]; e < g.tsv_ptr[i + 1]; ++e)
+            acc.term(key, g.tsv_eid[e], j0, g.sq_tsv[e], rk, g.tsv_sgn[e] <= 0);
+        for (int e = g.pad_ptr[i]; e < g.pad_ptr[i + 1]; ++e) acc.term(key, g.pad_eid[e], j0, g.sq_pad[e], rk, false);
+    }
+    reinterpret_cast<float4 *>(Yt + i * k + j0)[0] =
+        make_float4(__fadd_rn(acc.S[0], acc.C[0]), __fadd_rn(acc.S[1], acc.C[1]), __fadd_rn(acc.S[2], acc.C[2]),
+                    __fadd_rn(acc.S[3], acc.C[3]));
 }
 
 // Error-free transformations for FP32 dot products with FP64-class accuracy:
@@ -212,7 +285,7 @@ bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 void free_grid_arrays(er::GridDev &d) {
     void *ptrs[] = {d.cE64, d.cS64, d.cE32, d.cS32, d.dinvs, d.tsv_ptr, d.tsv_nbr, d.tsv_c64, d.tsv_c32,
                     d.gxr, d.gyr, d.tsv_eid, d.tsv_sgn, d.tsv_g, d.pad_ptr, d.pad_eid, d.pad_g, d.floating,
-                    d.coef32, d.tsv_g32, d.aux};
+                    d.coef32, d.tsv_g32, d.aux, d.sq_x, d.sq_y, d.sq_tsv, d.sq_pad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -382,6 +455,19 @@ er_status grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv, 
     UP(gxr, gxr); UP(gyr, gyr); UP(tsv_eid, teid); UP(tsv_sgn, tsgn); UP(tsv_g, tg);
     UP(pad_ptr, pcount); UP(pad_eid, peid); UP(pad_g, pg); UP(floating, floating);
     UP(coef32, coef); UP(tsv_g32, tg32);
+    {
+        // sqrt(w) as {hi, lo}: hi = sqrt(w) rounded to FP32, lo = the remainder rounded to FP32
+        auto pairs = [](const std::vector<double> &w) {
+            std::vector<float2> o(w.size());
+            for (size_t i = 0; i < w.size(); ++i) {
+                const double r = w[i] > 0.0 ? std::sqrt(w[i]) : 0.0;
+                const float h = (float)r;
+                o[i] = make_float2(h, (float)(r - (double)h));
+            }
+            return o;
+        };
+        UP(sq_x, pairs(gxr)); UP(sq_y, pairs(gyr)); UP(sq_tsv, pairs(tg)); UP(sq_pad, pairs(pg));
+    }
 #undef UP
     if (st == ER_OK) {
         cudaError_t e = cudaStreamSynchronize(stream);
@@ -405,6 +491,7 @@ SketchView sketch_view(const GridDev &d) {
     v.T = d.T; v.W = d.W; v.H = d.H; v.n = d.n; v.ex_slots = d.ex_slots; v.ey_slots = d.ey_slots;
     v.gxr = d.gxr; v.gyr = d.gyr; v.tsv_ptr = d.tsv_ptr; v.tsv_eid = d.tsv_eid; v.tsv_sgn = d.tsv_sgn;
     v.tsv_g = d.tsv_g; v.pad_ptr = d.pad_ptr; v.pad_eid = d.pad_eid; v.pad_g = d.pad_g;
+    v.sq_x = d.sq_x; v.sq_y = d.sq_y; v.sq_tsv = d.sq_tsv; v.sq_pad = d.sq_pad;
     v.floating = d.floating;
     return v;
 }
@@ -432,8 +519,11 @@ er_status sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *
     const double rk = 1.0 / std::sqrt((double)k);
     if (prec == ER_FP64)
         k_sketch<double><<<blocks, 256, 0, s>>>(sketch_view(d), k, key, rk, (double *)Yt);
-    else
-        k_sketch<float><<<blocks, 256, 0, s>>>(sketch_view(d), k, key, rk, (float *)Yt);
+    else {
+        const float rk_hi = (float)rk;
+        const float2 rk2 = make_float2(rk_hi, (float)(rk - (double)rk_hi));
+        k_sketch32<<<blocks, 256, 0, s>>>(sketch_view(d), k, key, rk2, (float *)Yt);
+    }
     ER_CUDA(cudaGetLastError());
     return ER_OK;
 }

@@ -70,6 +70,10 @@ struct GridDev {
     int32_t *pad_ptr = nullptr;             // n + 1
     int64_t *pad_eid = nullptr;
     double *pad_g = nullptr;
+    // FP32 sketch: square roots of the same conductances as {hi, lo} FP32 pairs (hi + lo
+    // carries about 48 bits), so the FP32 sketch needs no FP64 arithmetic
+    float2 *sq_x = nullptr, *sq_y = nullptr;  // per node, as gxr, gyr
+    float2 *sq_tsv = nullptr, *sq_pad = nullptr;  // per TSV / pad CSR entry
     uint8_t *floating = nullptr;
     struct Workspace *ws = nullptr;         // cached solve workspace (er_pcg.cu)
     void *aux = nullptr;                    // pairwise R / IR drop scratch (er_pairs.cu)

@@ -193,9 +193,54 @@ __device__ __forceinline__ TileGeo tile_geo(const Lvl &C, int k, int &tile) {
     return g;
 }
 
+// Per-column CTA partials of the CG dot products.  Thread q holds FP32 runs for the 4
+// columns of group q % 8; the 32 threads that share a group are summed in a fixed tree order
+// in double-float arithmetic (TwoSum, Knuth: s + e = a + b exactly), first across the four
+// lanes of a warp (shuffles), then across the 8 warps; one FP64 value per column is written.
+// FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU: an FP64 sum here cost a large
+// share of each tile kernel's duration.
+__device__ __forceinline__ float2 mg_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 df_plus(float2 a, float2 b) {  // (hi, lo) + (hi, lo)
+    const float2 t = mg_two_sum(a.x, b.x);
+    return mg_two_sum(t.x, __fadd_rn(t.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ void cta_col_partials(const float2 (&run)[4], int k, int c0, int tile, double *part) {
+    __shared__ float2 sred[8][32];  // [warp][column within the CTA's 32]
+    float2 v4[4] = {run[0], run[1], run[2], run[3]};
+#pragma unroll
+    for (int off = 8; off <= 16; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v4[v].x, off),
+                                         __shfl_xor_sync(0xffffffffu, v4[v].y, off));
+            v4[v] = (threadIdx.x & off) ? df_plus(o, v4[v]) : df_plus(v4[v], o);  // same order on both lanes
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane < 8)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sred[w][lane * 4 + v] = v4[v];
+    __syncthreads();
+    if (threadIdx.x < TCB) {
+        float2 acc = sred[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) acc = df_plus(acc, sred[q][threadIdx.x]);
+        const int col = c0 + threadIdx.x;
+        if (col < k) part[(int64_t)tile * k + col] = (double)acc.x + (double)acc.y;
+    }
+}
+__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, int tile, double *part) {
+    const float2 r2[4] = {make_float2(run[0], 0.f), make_float2(run[1], 0.f), make_float2(run[2], 0.f),
+                          make_float2(run[3], 0.f)};
+    cta_col_partials(r2, k, c0, tile, part);
+}
+
 // prolongation + post-sweep (UP) or pre-sweep + restriction (!UP) over one tile
 template <bool UP, bool DOT>
-__global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtensorMap mr,
+__global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUtensorMap mr,
                                                  const __grid_constant__ CUtensorMap mc,
                                                  const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
                                                  const float *__restrict__ r, const float *__restrict__ zc,
@@ -238,13 +283,22 @@ __global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtenso
             return v;
         };
         float4 acc = zero4();
+        // the smoothed field at the aggregate's own four nodes, computed once: each is the
+        // centre of one stencil and a neighbour in two others (only the ring outside the
+        // aggregate is evaluated per use, once each)
+        const int lx0 = 1 + 2 * ax, ly0 = 1 + 2 * ay;
+        float4 sv[2][2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) sv[dy][dx] = sval(ly0 + dy, lx0 + dx);
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
                 const int x = 2 * X + dx, y = 2 * Y + dy;
                 if (x >= F.W || y >= F.H) continue;
-                const int lx = 1 + 2 * ax + dx, ly = 1 + 2 * ay + dy;
+                const int lx = lx0 + dx, ly = ly0 + dy;
                 const float4 c = cs[ly * TFX + lx];
                 const int i = (g.t * F.H + y) * F.W + x;
                 if (c.x == 0.f) {  // floating node: not in P, z = 0
@@ -252,17 +306,17 @@ __global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtenso
                     continue;
                 }
                 const float4 ri = *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
-                const float4 vi = sval(ly, lx);
+                const float4 vi = sv[dy][dx];
                 float4 gv = c.w * vi;
-                if (c.y != 0.f) gv = fma4(c.y, vi - sval(ly, lx + 1), gv);
+                if (c.y != 0.f) gv = fma4(c.y, vi - (dx == 0 ? sv[dy][1] : sval(ly, lx + 1)), gv);
                 {
                     const float gw = cs[ly * TFX + lx - 1].y;
-                    if (gw != 0.f) gv = fma4(gw, vi - sval(ly, lx - 1), gv);
+                    if (gw != 0.f) gv = fma4(gw, vi - (dx == 1 ? sv[dy][0] : sval(ly, lx - 1)), gv);
                 }
-                if (c.z != 0.f) gv = fma4(c.z, vi - sval(ly + 1, lx), gv);
+                if (c.z != 0.f) gv = fma4(c.z, vi - (dy == 0 ? sv[1][dx] : sval(ly + 1, lx)), gv);
                 {
                     const float gn = cs[(ly - 1) * TFX + lx].z;
-                    if (gn != 0.f) gv = fma4(gn, vi - sval(ly - 1, lx), gv);
+                    if (gn != 0.f) gv = fma4(gn, vi - (dy == 1 ? sv[0][dx] : sval(ly - 1, lx)), gv);
                 }
                 if (c.x < 0.f) {
                     const int32_t e1 = F.tsv_ptr[i + 1];
@@ -287,18 +341,10 @@ __global__ void __launch_bounds__(256) k_mg_tile(const __grid_constant__ CUtenso
         if constexpr (!UP) f4st(out + (int64_t)J * k + col, acc);
     }
     if constexpr (DOT) {
-        // per column: the 64 items of the tile that share it, summed in a fixed order
-        __shared__ double sred[256 * 4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) sred[threadIdx.x * 4 + v] = (double)run[0][v] + (double)run[1][v];
-        __syncthreads();
-        if (threadIdx.x < TCB) {
-            const int cg = threadIdx.x >> 2, v = threadIdx.x & 3;
-            double sacc = 0.0;
-            for (int q = cg; q < 256; q += 8) sacc += sred[q * 4 + v];
-            const int col = g.c0 + threadIdx.x;
-            if (col < k) part[(int64_t)tile * k + col] = sacc;
-        }
+        // per column: the 64 items of the tile that share it (two per thread), summed in a fixed order
+        const float2 r2[4] = {mg_two_sum(run[0][0], run[1][0]), mg_two_sum(run[0][1], run[1][1]),
+                              mg_two_sum(run[0][2], run[1][2]), mg_two_sum(run[0][3], run[1][3])};
+        cta_col_partials(r2, k, g.c0, tile, part);
     }
 }
 
@@ -365,24 +411,8 @@ __device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int &tile) {  // 
     return g;
 }
 
-// per column: the items of the CTA that share it (thread q holds 4 columns of group q % 8),
-// summed in a fixed order
-__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, int tile, double *part) {
-    __shared__ double sred[256 * 4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) sred[threadIdx.x * 4 + v] = (double)run[v];
-    __syncthreads();
-    if (threadIdx.x < TCB) {
-        const int cg = threadIdx.x >> 2, v = threadIdx.x & 3;
-        double acc = 0.0;
-        for (int q = cg; q < 256; q += 8) acc += sred[q * 4 + v];
-        const int col = c0 + threadIdx.x;
-        if (col < k) part[(int64_t)tile * k + col] = acc;
-    }
-}
-
 // p' = z + beta p over the tile; partials of p'.G p' in edge form (pad, east, south, half TSV)
-__global__ void __launch_bounds__(256) k_mg_dir_tile(const __grid_constant__ CUtensorMap mzt,
+__global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ CUtensorMap mzt,
                                                      const __grid_constant__ CUtensorMap mpt,
                                                      const __grid_constant__ CUtensorMap mct, Lvl F, int k,
                                                      const float *__restrict__ z, const float *__restrict__ p,
@@ -525,30 +555,38 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
 }
 
 // coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
-// zero rows and columns at floating nodes) computed once on the host; one thread per node and
-// 4 columns, the inverse's row i read once per thread, r's rows shared through L1/L2
-__global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, Lay l, const float *__restrict__ ainv,
+// zero rows and columns at floating nodes) computed once on the host.  A dense product
+// [n_c x ld] x [ld x k]: each CTA owns a 32-row x 32-column tile of z and stages 32 columns
+// of the inverse's rows and 32 rows of r through shared memory at a time; a thread owns
+// one row and 4 columns (two accumulators, even and odd j).  ld % 4 == 0; the inverse's
+// columns n_c .. ld-1 are zero and r has ld rows (rows n_c .. ld-1 zero).
+constexpr int CI_T = 32;
+dim3 cinv_grid(int64_t n, int k) { return dim3((unsigned)((n + CI_T - 1) / CI_T), (unsigned)((k + CI_T - 1) / CI_T)); }
+
+__global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, const float *__restrict__ ainv,
                                                  const float *__restrict__ r, float *__restrict__ z) {
-    const int cgl = threadIdx.x % l.TPN, nl = threadIdx.x / l.TPN;
-    const int cg = blockIdx.y * l.TPN + cgl;
-    if (cg >= l.KG) return;
-    const int col = cg * 4;
-    const int i0 = blockIdx.x * l.NPS * l.steps + nl;
-    const int i1 = min(n, (blockIdx.x + 1) * l.NPS * l.steps);
-    for (int i = i0; i < i1; i += l.NPS) {
-        const float4 *row = reinterpret_cast<const float4 *>(ainv + (int64_t)i * ld);  // ld % 4 == 0, zero padded
-        float4 a0 = zero4(), a1 = zero4(), a2 = zero4(), a3 = zero4();
-#pragma unroll 4
-        for (int j4 = 0; j4 < ld / 4; ++j4) {
-            const float4 w = row[j4];
-            const int64_t o = (int64_t)(4 * j4) * k + col;
-            a0 = fma4(w.x, f4ld(r + o), a0);
-            a1 = fma4(w.y, f4ld(r + o + k), a1);
-            a2 = fma4(w.z, f4ld(r + o + 2 * k), a2);
-            a3 = fma4(w.w, f4ld(r + o + 3 * k), a3);
+    __shared__ __align__(16) float As[CI_T][CI_T + 4];  // [row][j], rows padded against bank conflicts
+    __shared__ __align__(16) float Rs[CI_T][CI_T];      // [j][column]
+    const int row0 = blockIdx.x * CI_T, col0 = blockIdx.y * CI_T;
+    const int ty = threadIdx.x >> 3, tx = (threadIdx.x & 7) * 4;  // this thread: row ty, columns tx .. tx+3
+    float4 a0 = zero4(), a1 = zero4();
+    for (int j0 = 0; j0 < ld; j0 += CI_T) {
+        {
+            const bool ok = row0 + ty < n && j0 + tx < ld;  // tx doubles as the j offset here
+            *reinterpret_cast<float4 *>(&As[ty][tx]) =
+                ok ? *reinterpret_cast<const float4 *>(ainv + (int64_t)(row0 + ty) * ld + j0 + tx) : zero4();
+            const bool okr = j0 + ty < ld && col0 + tx < k;  // ty doubles as the row of r
+            *reinterpret_cast<float4 *>(&Rs[ty][tx]) = okr ? f4ld(r + (int64_t)(j0 + ty) * k + col0 + tx) : zero4();
         }
-        f4st(z + (int64_t)i * k + col, (a0 + a1) + (a2 + a3));
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < CI_T; jj += 2) {
+            a0 = fma4(As[ty][jj], *reinterpret_cast<const float4 *>(&Rs[jj][tx]), a0);
+            a1 = fma4(As[ty][jj + 1], *reinterpret_cast<const float4 *>(&Rs[jj + 1][tx]), a1);
+        }
+        __syncthreads();
     }
+    if (row0 + ty < n && col0 + tx < k) f4st(z + (int64_t)(row0 + ty) * k + col0 + tx, a0 + a1);
 }
 
 // ---- per-column folds (one CTA per column, partials summed in a fixed tree order) -------
@@ -962,9 +1000,8 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
                   h.r[l + 1], (double *)nullptr, m.err);
     }
     const Lvl &C = h.lv[L - 1];
-    const Lay lco = make_lay(C.n, k);
-    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, dim3((unsigned)lco.chunks, lco.ncb), 0, (int)C.n, h.ld_inv, k, lco,
-              (const float *)h.ainv, (const float *)h.r[L - 1], h.z[L - 1]);
+    mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, cinv_grid(C.n, k), 0, (int)C.n, h.ld_inv, k, (const float *)h.ainv,
+              (const float *)h.r[L - 1], h.z[L - 1]);
     for (int l = L - 2; l >= 0; --l) {
         const float *rl = l == 0 ? r0 : h.r[l];
         if (l == 0)
@@ -1052,7 +1089,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     pf.on = opt.profile != 0;
     const bool use_graph = opt.use_graph && !pf.on;
     ER_CUDA(cudaMemsetAsync(w.ints + w.k + w.til.n_colblk, 0, sizeof(int), w.s));  // error word
-    fp32_init(g, w, Yt, Z, tol, &pf);  // r = b, x = 0, p = 0, x64 = 0; rho0 = rho = b.D^-1 b; active
+    fp32_init(g, w, Yt, Z, tol, &pf);  // r = b, x = 0, p = 0, xhl = 0; rho0 = rho = b.D^-1 b; active
     ER_CUDA(cudaGetLastError());
 
     auto poll = [&](int *vals) -> er_status {
@@ -1065,7 +1102,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
         vals[2] = w.h_poll[0];
         return ER_OK;
     };
-    // FP64 residual replacement: x64 += x, x = 0, r = b - G x64 (FP64); freeze columns at tol
+    // accurate residual replacement: xhl += x, x = 0, r = b - G xhl (double-float); freeze columns at tol
     auto replace = [&](int *n_active) -> er_status {
         fp32_accum(g, w, Z, &pf);
         fp32_residual(g, w, Yt, tol, 0, 0, &pf);

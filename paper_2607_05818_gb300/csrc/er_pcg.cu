@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_stream(const KArgs<T, T> a) {
 void free_workspace(GridDev *g) {
     Workspace *w = g->ws;
     if (!w) return;
-    void *ptrs[] = {w->r[0], w->r[1], w->p[0], w->p[1], w->q, w->x64, w->part, w->scal, w->ints, w->counter};
+    void *ptrs[] = {w->r[0], w->r[1], w->p[0], w->p[1], w->q, w->xhl, w->part, w->scal, w->ints, w->counter};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w->h_poll) cudaFreeHost(w->h_poll);
@@ -314,7 +314,7 @@ static er_status get_workspace(GridDev *g, int k, er_precision prec, int rows, i
         ER_CUDA(cudaMalloc(&w->q, vec));
     } else {
         ER_CUDA(cudaMalloc(&w->r[1], vec));
-        ER_CUDA(cudaMalloc((void **)&w->x64, (size_t)g->n * (size_t)k * sizeof(double)));
+        ER_CUDA(cudaMalloc((void **)&w->xhl, (size_t)g->n * (size_t)k * sizeof(float2)));
     }
     ER_CUDA(cudaMalloc(&w->part, (size_t)w->til.n_spatial * k * sizeof(double)));
     ER_CUDA(cudaMalloc(&w->scal, (size_t)6 * k * sizeof(double)));
