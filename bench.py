@@ -205,8 +205,10 @@ def ncu_traffic(kernel, workload):
 
 
 def run_batch(args, rank, world, local_rank):
-    """Batching form: 512 TSV-placement candidates (k = 64) in shared launches, against the
-    same candidates solved one after another (er_solve per candidate, warm workspace)."""
+    """Batching form: 512 TSV-placement candidates (k = 64) through er_batch_solve, with the
+    multigrid preconditioner (concurrent per-network solves; the default, --precond mg) or
+    Jacobi (shared launches), the other mode timed once beside it, against the same
+    candidates solved one after another (er_solve per candidate, warm workspace)."""
     import torch
     from paper_2607_05818_gb300 import er
     from paper_2607_05818_gb300 import instances as I
@@ -220,15 +222,19 @@ def run_batch(args, rank, world, local_rank):
     n_ok = sum(i["n_nodes"] - i["n_floating"] for i in infos)
     R = [torch.empty(c.n, dtype=torch.float64, device=dev) for c in cands]
     opts = er.default_solve_opts("fp32")
+    opts_mg = er.default_solve_opts("fp32", precond=1, check_every=2)
     if args.tol is not None:
         opts.tol = args.tol
+        opts_mg.tol = args.tol
+    use_mg = args.precond == "mg"
+    opts_run, opts_other = (opts_mg, opts) if use_mg else (opts, opts_mg)
     rows = None
     if args.autotune:
         from paper_2607_05818_gb300 import autotune
         rows = [autotune.best_rows(c, k) for c in cands]
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        er.batch_solve(grids, k, 1, R, opts=opts, tile_rows=rows)
+        er.batch_solve(grids, k, 1, R, opts=opts_run, tile_rows=rows)
     torch.cuda.synchronize()
     stats = []
     with ClockSampler(gpu_index(local_rank)) as clk:
@@ -239,7 +245,7 @@ def run_batch(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            stats.append(er.batch_solve(grids, k, 1, R, opts=opts, tile_rows=rows)[1])
+            stats.append(er.batch_solve(grids, k, 1, R, opts=opts_run, tile_rows=rows)[1])
         e1.record(stream)
         if world > 1:
             torch.distributed.barrier()
@@ -247,14 +253,16 @@ def run_batch(args, rank, world, local_rank):
     n_job, s_max = combine_ranks(n_ok, e0.elapsed_time(e1) / 1e3, world, dev)
     ms = 1e3 * s_max
     value = n_job * args.steps / s_max
+    # the other mode of er_batch_solve, one call (outside the timed region)
+    o0 = time.perf_counter()
+    st_other = er.batch_solve(grids, k, 1, R, opts=opts_other, tile_rows=rows)[1]
+    torch.cuda.synchronize()
+    other_s = time.perf_counter() - o0
     # sequential: each candidate's sketch + solve + map on its own (second call, warm workspace),
     # with the batching form's Jacobi preconditioner and with the multigrid V-cycle
     nmax = max(c.n for c in cands)
     Y = torch.empty(nmax * k, dtype=torch.float32, device=dev)
     Z = torch.empty_like(Y)
-    opts_mg = er.default_solve_opts("fp32", precond=1, check_every=2)
-    if args.tol is not None:
-        opts_mg.tol = args.tol
     seq_ms, seq_mg_ms = 0.0, 0.0
     for c, (cand, g) in enumerate(zip(cands, grids)):
         y = Y[: cand.n * k].view(cand.n, k)
@@ -286,7 +294,13 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": f"batch_candidates_{len(cands)}", "k": k, "candidates": len(cands),
                    "nodes": n_ok, "iterations": last["iterations"], "converged": last["converged"],
                    "graph_captures": last["graph_captures"], "tile_rows": "autotuned" if rows else "default 64",
-                   "max_rel_residual": last["max_rel_residual"]},
+                   "max_rel_residual": last["max_rel_residual"],
+                   "mode": "multigrid: concurrent per-network solves on 8 worker streams" if use_mg
+                   else "Jacobi: shared launches over a (network, tile) work list"},
+        "other_mode": {"mode": "Jacobi shared launches" if use_mg else "multigrid concurrent solves",
+                       "value": n_ok / other_s, "unit": UNIT, "seconds": other_s,
+                       "iterations": st_other["iterations"], "converged": st_other["converged"],
+                       "note": "one er_batch_solve call, host wall time"},
         "sequential": {"value": seq_value, "unit": UNIT, "ms": seq_ms,
                        "note": "er_sketch + er_solve + er_reff_map per candidate, warm workspace, Jacobi"},
         "sequential_multigrid": {"value": seq_mg_value, "unit": UNIT, "ms": seq_mg_ms,

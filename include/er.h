@@ -218,13 +218,20 @@ typedef struct {
 } er_batch_stats;
 
 /* Batching form: the all-node R maps of n networks (e.g. TSV-placement candidates of
- * uneven sizes) in shared launches.  Network c is sketched with seed + c, solved in the
- * FP32 form (the arithmetic of er_solve with ER_FP32_REFINE) and its map written to the
- * device array R_out[c] [n_c] (FP64).  Every pass of every iteration is ONE launch over a
- * work list of (network, tile) pairs, captured in a CUDA graph per poll period; networks
- * leave the work list as they converge.  tile_rows[c] (nullable) overrides the y rows
- * swept per CTA for network c (the autotuner's choice).  prec must be ER_FP32_REFINE.
- * Workspace is allocated for the call and freed before it returns.  Synchronises. */
+ * uneven sizes).  Network c is sketched with seed + c, solved in the FP32 form (the
+ * arithmetic of er_solve with ER_FP32_REFINE) and its map written to the device array
+ * R_out[c] [n_c] (FP64).  prec must be ER_FP32_REFINE.  Synchronises.
+ *   opts->precond == 0 (Jacobi, the default): shared launches.  Every pass of every
+ *     iteration is ONE launch over a work list of (network, tile) pairs, captured in a CUDA
+ *     graph per poll period; networks leave the work list as they converge.  tile_rows[c]
+ *     (nullable) overrides the y rows swept per CTA for network c (the autotuner's choice).
+ *     Workspace is allocated for the call and freed before it returns.
+ *   opts->precond == 1 (multigrid): each network runs er_sketch + er_solve (multigrid
+ *     V-cycle) + er_reff_map exactly as alone, on up to 8 host worker threads with one
+ *     stream each, largest networks first, so small networks overlap on the GPU.  Each
+ *     grid keeps its solve workspace and hierarchy cached (as after er_solve); a grid may
+ *     appear only once (ER_ERR_INVALID_ARG otherwise); tile_rows is ignored.  On a hard
+ *     error the remaining networks are skipped and the first error is returned. */
 er_status er_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, er_precision prec,
                          const int32_t *tile_rows, double *const *R_out, const er_solve_opts *opts,
                          er_batch_stats *stats, void *stream);

@@ -50,7 +50,7 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SRC)) as ex:
         logs = list(ex.map(lambda a: _compile(*a, extra), zip(SRC, objs)))
     tmp = LIB + ".tmp"
-    r = subprocess.run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    r = subprocess.run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -39,6 +39,7 @@
 // reports ER_ERR_TIMEOUT.
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -638,12 +639,12 @@ er_status fp32_make_map(CUtensorMap *m, bool f64, const void *base, int64_t d0, 
                : make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, d0, box0, g);
 }
 
-static bool g_attr_done = false;
-static bool g_battr_done = false;
+static std::atomic<bool> g_attr_done{false};  // set once; solves may run on several host threads
+static std::atomic<bool> g_battr_done{false};
 
 er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, int n_work, int cur, int rmode,
                           cudaStream_t s) {
-    if (!g_battr_done) {
+    if (!g_battr_done.load()) {
         ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_A_DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_A_DOT>()));
         ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -652,7 +653,7 @@ er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, in
                                      dyn_smem<MODE_B0>()));
         ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_R>()));
-        g_battr_done = true;
+        g_battr_done.store(true);
     }
     if (n_work <= 0) return ER_OK;
     const unsigned nb = (unsigned)n_work;
@@ -692,7 +693,7 @@ er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z) 
         if (s != ER_OK) return s;
         w.tm_b_ptr = Yt;
     }
-    if (!g_attr_done) {
+    if (!g_attr_done.load()) {
         ER_CUDA(cudaFuncSetAttribute(k_tma<MODE_A_DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_A_DOT>()));
         ER_CUDA(cudaFuncSetAttribute(k_tma<MODE_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -701,7 +702,7 @@ er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z) 
                                      dyn_smem<MODE_B0>()));
         ER_CUDA(cudaFuncSetAttribute(k_tma<MODE_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_R>()));
-        g_attr_done = true;
+        g_attr_done.store(true);
     }
     return ER_OK;
 }

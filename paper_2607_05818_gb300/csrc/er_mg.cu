@@ -31,6 +31,7 @@
 // Small per-column folds sum per-CTA partials in a fixed order (results are identical from
 // run to run).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -196,7 +197,7 @@ __device__ __forceinline__ TileGeo tile_geo(const Lvl &C, int k, int &tile) {
 // Per-column CTA partials of the CG dot products.  Thread q holds FP32 runs for the 4
 // columns of group q % 8; the 32 threads that share a group are summed in a fixed tree order
 // in double-float arithmetic (TwoSum, Knuth: s + e = a + b exactly), first across the four
-// lanes of a warp (shuffles), then across the 8 warps; one FP64 value per column is written.
+// lanes of a warp (shuffles), then across the 8 warps; one {hi, lo} pair per column is written.
 // FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU: an FP64 sum here cost a large
 // share of each tile kernel's duration.
 __device__ __forceinline__ float2 mg_two_sum(float a, float b) {
@@ -208,7 +209,7 @@ __device__ __forceinline__ float2 df_plus(float2 a, float2 b) {  // (hi, lo) + (
     const float2 t = mg_two_sum(a.x, b.x);
     return mg_two_sum(t.x, __fadd_rn(t.y, __fadd_rn(a.y, b.y)));
 }
-__device__ __forceinline__ void cta_col_partials(const float2 (&run)[4], int k, int c0, int tile, double *part) {
+__device__ __forceinline__ void cta_col_partials(const float2 (&run)[4], int k, int c0, int tile, float2 *part) {
     __shared__ float2 sred[8][32];  // [warp][column within the CTA's 32]
     float2 v4[4] = {run[0], run[1], run[2], run[3]};
 #pragma unroll
@@ -229,10 +230,10 @@ __device__ __forceinline__ void cta_col_partials(const float2 (&run)[4], int k, 
 #pragma unroll
         for (int q = 1; q < 8; ++q) acc = df_plus(acc, sred[q][threadIdx.x]);
         const int col = c0 + threadIdx.x;
-        if (col < k) part[(int64_t)tile * k + col] = (double)acc.x + (double)acc.y;
+        if (col < k) part[(int64_t)tile * k + col] = acc;
     }
 }
-__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, int tile, double *part) {
+__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, int tile, float2 *part) {
     const float2 r2[4] = {make_float2(run[0], 0.f), make_float2(run[1], 0.f), make_float2(run[2], 0.f),
                           make_float2(run[3], 0.f)};
     cta_col_partials(r2, k, c0, tile, part);
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUte
                                                  const __grid_constant__ CUtensorMap mc,
                                                  const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
                                                  const float *__restrict__ r, const float *__restrict__ zc,
-                                                 float *__restrict__ out, double *part, int *err) {
+                                                 float *__restrict__ out, float2 *part, int *err) {
     extern __shared__ unsigned char mg_tile_raw[];
     __shared__ __align__(8) uint64_t bar;
     unsigned char *sm = mg_tile_raw + ((128u - (mg_saddr(mg_tile_raw) & 127u)) & 127u);
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ 
                                                      const __grid_constant__ CUtensorMap mct, Lvl F, int k,
                                                      const float *__restrict__ z, const float *__restrict__ p,
                                                      const double *__restrict__ beta, float *__restrict__ p_out,
-                                                     double *part, int *err) {
+                                                     float2 *part, int *err) {
     extern __shared__ unsigned char mg_dir_raw[];
     __shared__ __align__(8) uint64_t bar;
     unsigned char *sm = mg_dir_raw + ((128u - (mg_saddr(mg_dir_raw) & 127u)) & 127u);
@@ -432,14 +433,14 @@ __global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ 
         mg_tma4(sm + S_V, &mpt, &bar, g.c0, g.x0, g.y0, g.t);
         mg_tma4(sm + 2 * S_V, &mct, &bar, 0, g.x0, g.y0, g.t);
     }
+    __shared__ __align__(16) float s_b[TCB];  // beta in FP32, one conversion per column
+    if (threadIdx.x < TCB) s_b[threadIdx.x] = g.c0 + (int)threadIdx.x < k ? (float)beta[g.c0 + threadIdx.x] : 0.f;
     __syncthreads();
     if (!ctile_wait(&bar, err)) return;
     float run[4] = {0.f, 0.f, 0.f, 0.f};
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
-    const float4 b4 = col < k ? make_float4((float)beta[col], (float)beta[col + 1], (float)beta[col + 2],
-                                            (float)beta[col + 3])
-                              : zero4();
+    const float4 b4 = *reinterpret_cast<const float4 *>(s_b + cg * 4);
     auto sv = [&](int ly, int lx) {
         const int o = (ly * SPX + lx) * TCB + cg * 4;
         return (b4 * *reinterpret_cast<const float4 *>(ps + o)) + *reinterpret_cast<const float4 *>(zs + o);
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
                                                      const double *__restrict__ alpha,
                                                      const double *__restrict__ alpha_prev,
                                                      const float *__restrict__ p, const float *__restrict__ p_prev,
-                                                     float *__restrict__ x, float *__restrict__ r, double *part,
+                                                     float *__restrict__ x, float *__restrict__ r, float2 *part,
                                                      int *err) {
     extern __shared__ unsigned char mg_upd_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -501,16 +502,21 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
         mg_tma4(sm, &mpt, &bar, g.c0, g.x0 - 1, g.y0 - 1, g.t);
         mg_tma4(sm + U_V, &mct, &bar, 0, g.x0 - 1, g.y0 - 1, g.t);
     }
+    // the CTA's 32 step lengths, converted to FP32 once per column (an FP64 -> FP32
+    // conversion runs on the FP64 pipe: one per thread and column kept it 18% busy)
+    __shared__ __align__(16) float s_a[TCB], s_ap[TCB];
+    if (threadIdx.x < TCB) {
+        const int j = g.c0 + threadIdx.x;
+        s_a[threadIdx.x] = j < k ? (float)alpha[j] : 0.f;
+        if constexpr (XPAIR) s_ap[threadIdx.x] = j < k ? (float)alpha_prev[j] : 0.f;
+    }
     __syncthreads();
     if (!ctile_wait(&bar, err)) return;
     float run[4] = {0.f, 0.f, 0.f, 0.f};
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
-    auto ld4d = [&](const double *a) {
-        return col < k ? make_float4((float)a[col], (float)a[col + 1], (float)a[col + 2], (float)a[col + 3]) : zero4();
-    };
-    const float4 a4 = ld4d(alpha);
-    const float4 ap4 = XPAIR ? ld4d(alpha_prev) : zero4();
+    const float4 a4 = *reinterpret_cast<const float4 *>(s_a + cg * 4);
+    const float4 ap4 = XPAIR ? *reinterpret_cast<const float4 *>(s_ap + cg * 4) : zero4();
     auto pv_at = [&](int ly, int lx) {
         return *reinterpret_cast<const float4 *>(ps + (ly * UPX + lx) * TCB + cg * 4);
     };
@@ -594,7 +600,7 @@ __global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, const flo
 enum { FOLD_ALPHA = 0, FOLD_RR = 1, FOLD_BETA = 2 };
 
 struct FoldArgs {
-    const double *part;
+    const float2 *part;  // per-CTA partials as double-float {hi, lo}
     int64_t chunks;
     int k;
     double *alpha, *beta, *rho, *rho0;
@@ -607,18 +613,18 @@ struct FoldArgs {
 
 template <int KIND>
 __global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
-    __shared__ double s[256];
+    __shared__ float2 s[256];
     const int j = blockIdx.x;
-    double acc = 0.0;
-    for (int64_t c = threadIdx.x; c < f.chunks; c += blockDim.x) acc += f.part[c * f.k + j];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int64_t c = threadIdx.x; c < f.chunks; c += blockDim.x) acc = df_plus(acc, f.part[c * f.k + j]);
     s[threadIdx.x] = acc;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        if (threadIdx.x < w) s[threadIdx.x] = df_plus(s[threadIdx.x], s[threadIdx.x + w]);
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    const double tot = s[0];
+    const double tot = (double)s[0].x + (double)s[0].y;
     const bool act = f.active[j] != 0;
     if constexpr (KIND == FOLD_ALPHA) {
         f.alpha_prev[j] = f.alpha[j];
@@ -703,7 +709,7 @@ struct MgHier {
     // tiled CG passes on the finest level: direction (z, p[0], p[1], coefficients; east/south
     // halo) and update (p[0], p[1], coefficients; halo on every side)
     CUtensorMap dmap_z, dmap_p[2], dmap_c, umap_p[2], umap_c;
-    double *part = nullptr;
+    float2 *part = nullptr;
     int64_t part_chunks = 0;
     int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
     int *h_cnt = nullptr;          // pinned host copy
@@ -943,7 +949,7 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
         h->part_chunks = std::max(std::max(make_lay(g.n, k).chunks, n_tiles(h->lv[1])), n_ctiles(h->lv[0]));
         if (h->msc) cudaFree(h->msc);
         ER_CUDA(cudaMalloc(&h->msc, (size_t)2 * k * sizeof(double)));
-        ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(double)));
+        ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(float2)));
         h->k = k;
     }
     *out = h;
@@ -997,7 +1003,7 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
         const float *rl = l == 0 ? r0 : h.r[l];
         mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_tile<false, false>, tile_grid(h.lv[l + 1], k),
                   T_SMEM, h.map_r[l], h.map_c[l], h.map_r[l], h.lv[l], h.lv[l + 1], k, rl, (const float *)nullptr,
-                  h.r[l + 1], (double *)nullptr, m.err);
+                  h.r[l + 1], (float2 *)nullptr, m.err);
     }
     const Lvl &C = h.lv[L - 1];
     mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, cinv_grid(C.n, k), 0, (int)C.n, h.ld_inv, k, (const float *)h.ainv,
@@ -1010,7 +1016,7 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
         else
             mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<true, false>, tile_grid(h.lv[l + 1], k), T_SMEM, h.map_r[l],
                       h.map_c[l], h.map_z[l + 1], h.lv[l], h.lv[l + 1], k, rl, (const float *)h.z[l + 1], h.z[l],
-                      (double *)nullptr, m.err);
+                      (float2 *)nullptr, m.err);
     }
     mg_launch(*m.w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_BETA>, dim3((unsigned)k), 0, fold_args(m, n_tiles(h.lv[1])));
 }
@@ -1073,15 +1079,15 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
         if (ms == ER_OK) ms = mg_map(&h->dmap_c, L0.coef, 4, L0, 4, SPX, SPY);
         if (ms == ER_OK) ms = mg_map(&h->umap_c, L0.coef, 4, L0, 4, UPX, UPY);
         if (ms != ER_OK) return ms;
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<bool> attr{false};  // solves of different grids may run on several threads
+        if (!attr.load()) {
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_dir_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
-            attr = true;
+            attr.store(true);
         }
     }
     MgRun m{&g, &w, h, k, tol, Z, w.ints + w.k + w.til.n_colblk};

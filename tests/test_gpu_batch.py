@@ -76,3 +76,35 @@ def test_batch_rejects_fp64_and_bad_args(er):
         er.batch_solve(grids, 30, 1, R)
     for g in grids:
         g.destroy()
+
+
+def test_multigrid_batch_equals_single_solves(er):
+    """precond = 1: every network is solved by er_solve's multigrid form (several at a time on
+    worker streams), so each map is bitwise the map of sketch + solve + map on that network
+    alone, and within the FP32 form's bound of the oracle."""
+    nets = make_batch()
+    k, seed = 32, 515
+    grids = [er.grid_create(n) for n in nets]
+    R = [torch.full((n.n,), float("nan"), dtype=torch.float64, device="cuda") for n in nets]
+    opts = er.default_solve_opts("fp32", precond=1, check_every=2)
+    s, st = er.batch_solve(grids, k, seed, R, opts=opts)
+    torch.cuda.synchronize()
+    assert st["n_grids"] == len(nets) and st["converged"] == len(nets)
+    assert st["nodes"] == sum(n.n - int(network.floating_mask(n).sum()) for n in nets)
+    for c, (net, g) in enumerate(zip(nets, grids)):
+        Y = torch.empty((net.n, k), dtype=torch.float32, device="cuda")
+        Z = torch.empty_like(Y)
+        R1 = torch.empty(net.n, dtype=torch.float64, device="cuda")
+        er.sketch(g, k, seed + c, "fp32", Y)
+        er.solve(g, Y, Z, k, "fp32", opts)
+        er.reff_map(g, Z, k, "fp32", R1)
+        torch.cuda.synchronize()
+        got, one = R[c].cpu().numpy(), R1.cpu().numpy()
+        assert np.array_equal(got, one), c  # +inf at floating nodes compares equal
+        ref, _ = osk.reff_jl_dense(net, k, seed + c)
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(got), fin)
+        if fin.any():
+            assert np.max(np.abs(got[fin] / ref[fin] - 1)) <= 1e-3, c
+    for g in grids:
+        g.destroy()

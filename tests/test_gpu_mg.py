@@ -112,7 +112,9 @@ def test_mg_option_rules(er):
         er.solve(g, Y, Z, 8, "fp64", er.default_solve_opts("fp64", precond=1))
     with pytest.raises(er.ErError):
         er.solve(g, Y.float(), Z.float(), 8, "fp32", er.default_solve_opts("fp32", precond=2))
-    R = [torch.empty(inst.n, dtype=torch.float64, device="cuda")]
-    with pytest.raises(er.ErError):
-        er.batch_solve([g], 8, 1, R, opts=er.default_solve_opts("fp32", precond=1))
+    R = [torch.empty(inst.n, dtype=torch.float64, device="cuda")] * 2
+    with pytest.raises(er.ErError):  # no such preconditioner
+        er.batch_solve([g], 8, 1, R[:1], opts=er.default_solve_opts("fp32", precond=2))
+    with pytest.raises(er.ErError):  # the multigrid batch solves networks concurrently: no grid twice
+        er.batch_solve([g, g], 8, 1, R, opts=er.default_solve_opts("fp32", precond=1))
     g.destroy()
