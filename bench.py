@@ -3,9 +3,10 @@
 One step = the whole hot path on one synthetic network already resident in HBM:
 JL sketch (er_sketch) + k-RHS Jacobi-PCG solve (er_solve) + R map (er_reff_map).
 Default workload: 4 tiers x 512x512 (1,048,576 nodes), k = 256, the FP32 form: FP32
-vectors and stencil, FP64-accumulated dots, an FP64 iterate with the FP64 residual
-substituted every 50 iterations (reliable updates), stopped at FP64 residual 1e-7, with the
-aggregation-multigrid V-cycle as preconditioner (--precond jacobi: Jacobi-PCG).
+vectors and stencil, double-float dot sums, a double-float iterate (pairs of FP32 numbers)
+with the accurate residual substituted every 50 iterations (reliable updates), stopped at an
+accurate residual of 1e-7, with the aggregation-multigrid V-cycle as preconditioner
+(--precond jacobi: Jacobi-PCG).
 
 Prints one JSON line (rank 0).  N > 1 (torchrun): every rank maps its own network
 (independent seeds) with no collective on the data path; value = all ranks' nodes /

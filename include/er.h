@@ -94,8 +94,8 @@ typedef struct {
     int32_t maxit;         /* iteration cap (both forms, all sweeps together) */
     int32_t check_every;   /* host convergence poll period in iterations (>= 1) */
     int32_t replace_every; /* ER_FP32_REFINE: every m iterations the FP32 correction is
-                              folded into the FP64 iterate and the FP64 residual replaces
-                              the recursive one (m >= 1) */
+                              folded into the accurate (double-float) iterate and the
+                              accurate residual replaces the recursive one (m >= 1) */
     int32_t use_graph;     /* 1: replay each poll period from a captured CUDA graph */
     int32_t profile;       /* 1: time every pass with CUDA events on the solver's stream
                               (disables graphs); fills er_solve_stats.kernel_ms */
@@ -110,8 +110,8 @@ typedef struct {
 enum { ER_PASS_A = 0,      /* stencil pass: p' = z + beta p, q = G p', dot p'.q */
        ER_PASS_B = 1,      /* update pass: x, r (and p' in the FP32 form), dot r.z; in the
                               FP32 form the odd iterations, which also update x */
-       ER_PASS_R = 2,      /* FP64 residual pass */
-       ER_PASS_OTHER = 3,  /* initialisation, FP64 accumulation of x, final Z */
+       ER_PASS_R = 2,      /* accurate residual pass (FP64 form: FP64; FP32 form: double-float) */
+       ER_PASS_OTHER = 3,  /* initialisation, accumulation of x into the accurate iterate, final Z */
        ER_PASS_B0 = 4,     /* FP32 form, even iterations: update pass without x */
        ER_PASS_MG = 5,     /* multigrid V-cycle kernels on the coarse levels (precond = 1) */
        ER_PASS_MG_DOWN = 6,/* multigrid: pre-sweep and restriction on the finest level */
@@ -120,17 +120,17 @@ enum { ER_PASS_A = 0,      /* stencil pass: p' = z + beta p, q = G p', dot p'.q 
 
 typedef struct {
     int32_t iterations;       /* PCG iterations run */
-    int32_t sweeps;           /* FP64 residual replacements (ER_FP32_REFINE) */
+    int32_t sweeps;           /* accurate residual replacements (ER_FP32_REFINE) */
     int32_t converged_cols;   /* columns meeting tol at the end */
     int32_t k;
-    double max_rel_residual;  /* final FP64 true residual, max over columns, same norm as tol */
+    double max_rel_residual;  /* final accurate true residual, max over columns, same norm as tol */
     double seconds;           /* host wall time of the call */
     int32_t launches[ER_N_PASS];  /* kernels launched, by pass kind */
     double kernel_ms[ER_N_PASS];  /* summed CUDA-event durations by pass kind (profile = 1) */
 } er_solve_stats;
 
-/* Default solve options: tol 1e-12 (FP64) / 1e-7 (FP32 form; the FP64 residual of the
- * FP64 iterate), maxit 20000, check_every 10, replace_every 50, use_graph 1,
+/* Default solve options: tol 1e-12 (FP64) / 1e-7 (FP32 form; the accurate residual of the
+ * accurate iterate), maxit 20000, check_every 10, replace_every 50, use_graph 1,
  * profile 0, tile_rows 0, block_order 0, precond 0. */
 er_solve_opts er_default_solve_opts(er_precision prec);
 
@@ -170,10 +170,13 @@ er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, voi
  * ER_FP64: FP64 throughout (run as CG on D^-1/2 G D^-1/2, identical iterates).
  * ER_FP32_REFINE: FP32 vectors, stencil and updates on the network with every
  * conductance rounded to FP32 once (which moves any R by at most a relative 2^-24);
- * dot products accumulated in FP64; every replace_every iterations the FP32
- * correction is added to an FP64 iterate and the residual is recomputed in FP64 and
- * substituted (reliable update, no restart); a column stops only when that FP64
- * residual meets tol.  Z is written in FP32.
+ * dot products accumulated in double-float and FP64; every replace_every iterations the
+ * FP32 correction is added to an accurate iterate and the residual is recomputed
+ * accurately and substituted (reliable update, no restart); a column stops only when that
+ * accurate residual meets tol.  "Accurate" is double-float arithmetic (pairs of FP32
+ * numbers, about 48 bits, error-free transformations): FP64 runs at 1/64 of the FP32 rate
+ * on GB300, and the residual's error (about 2^-44 of its terms) is far below any
+ * tolerance the FP32 form is meant for (>= 1e-10).  Z is written in FP32.
  * precond = 1 (FP32 form): the preconditioner is one V-cycle of an aggregation multigrid
  * instead of D^-1.  Level l+1 aggregates 2 x 2 nodes of every tier of level l; since the
  * Galerkin product P^T G P of a network's matrix is again a network (segments between
@@ -208,10 +211,10 @@ er_status er_solve_noalloc(er_grid *g, const void *Yt, void *Z, int32_t k, const
 typedef struct {
     int32_t n_grids;
     int32_t iterations;       /* iterations of the batch (the slowest network) */
-    int32_t replacements;     /* FP64 residual replacements */
+    int32_t replacements;     /* accurate residual replacements */
     int32_t converged;        /* networks whose every column met tol */
     int64_t nodes;            /* non-floating nodes over all networks */
-    double max_rel_residual;  /* final FP64 residual, max over all networks and columns */
+    double max_rel_residual;  /* final accurate residual, max over all networks and columns */
     double seconds;           /* host wall time of the call */
     int32_t launches;         /* kernels launched */
     int32_t graph_captures;   /* CUDA graphs captured (one per change of the work list) */

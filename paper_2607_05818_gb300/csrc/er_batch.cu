@@ -1,13 +1,14 @@
-// Batching form: the all-node R map of many uneven networks in shared launches.
+// Batching form: the all-node R map of many uneven networks, in shared launches
+// (Jacobi, precond 0; below) or as concurrent multigrid solves (precond 1; batch_solve_mg).
 //
 // Every network keeps its own grid (coefficients, TSV CSR), its own vectors and its own
-// per-column CG scalars, but each pass (A, B/B0, FP64 residual, initialisation,
+// per-column CG scalars, but each pass (A, B/B0, accurate residual, initialisation,
 // accumulation, final Z) is ONE launch over a work list of (network, block) pairs, so
 // small networks that could not fill the GPU alone run side by side.  A poll period of
 // iterations is captured once into a CUDA graph and replayed; when networks finish, the
 // work list shrinks and the graph is captured again.  The arithmetic is the FP32 form
-// of er_solve (FP32 Jacobi-PCG on the FP32-rounded network, FP64 iterate with the FP64
-// residual substituted every replace_every iterations, FP64 stopping test).
+// of er_solve (FP32 Jacobi-PCG on the FP32-rounded network, double-float iterate with
+// the accurate residual substituted every replace_every iterations, accurate stopping test).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -369,7 +370,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
             bool need = false;
             for (int c = 0; c < n; ++c) need |= live[c] && unconv[c] == 0;
             if (!need) continue;
-            st = replace();  // some network's recursion meets tol everywhere: the FP64 residual decides
+            st = replace();  // some network's recursion meets tol everywhere: the accurate residual decides
             if (st != ER_OK) return st;
             st = poll(act, &err);
         }
@@ -386,7 +387,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
         }
     }
     const bool done = !any_live();
-    // final: every network's correction folded in, FP64 residual recorded, Z, R
+    // final: every network's correction folded in, accurate residual recorded, Z, R
     std::fill(live.begin(), live.end(), 1);
     st = build_work();
     if (st == ER_OK) st = pass(MODE_ACCUM, 0, 0);

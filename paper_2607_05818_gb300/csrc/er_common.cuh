@@ -135,7 +135,7 @@ __device__ inline void finalize_column(const KArgs<T, C> &a, int j, double total
         a.resid[j] = rel;
         if (a.rmode == 1 && a.active[j]) {
             // reliable update: the recursion continues from the recomputed residual.  If the
-            // recursion already claims tol while the FP64 residual does not, or it has fallen
+            // recursion already claims tol while the accurate residual does not, or it has fallen
             // more than 100x below the true residual, it ran on past its attainable accuracy
             // and the search direction is stale: restart it (beta = 0, a refinement sweep on
             // the correction) instead of rescaling it.

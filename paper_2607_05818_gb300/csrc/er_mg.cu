@@ -20,10 +20,10 @@
 //     columns, staged with a one-node halo by cp.async.bulk.tensor; z0 is never stored, it is
 //     recomputed from r; the coarsest level (at most 512 nodes) is solved exactly by its dense
 //     inverse.
-// The CG recursion is the FP32 form's (FP32 vectors, FP64-accumulated dots, FP64 iterate
-// with the FP64 residual substituted every replace_every iterations, and whenever every
-// column's recursive residual meets tol; a column stops only when that FP64 residual meets
-// tol, and a column whose recursion ran past its attainable accuracy restarts its search
+// The CG recursion is the FP32 form's (FP32 vectors, double-float dot sums, double-float
+// iterate with the accurate residual substituted every replace_every iterations, and whenever
+// every column's recursive residual meets tol; a column stops only when that accurate residual
+// meets tol, and a column whose recursion ran past its attainable accuracy restarts its search
 // direction), in three stages per iteration: the V-cycle (whose last kernel also forms r.z),
 // p' = z + beta p with the energy p'.G p', and r -= alpha G p' with G p' recomputed from p'
 // (never stored) and r.D^-1 r; x takes two iterations' steps every second iteration.  The
@@ -645,9 +645,9 @@ __global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
     }
 }
 
-// after an FP64 residual replacement: freeze the columns whose FP64 residual meets tol and
-// count the rest.  A column whose recursive residual has run more than 100x below the FP64
-// one, or claims tol while the FP64 residual does not, has a stale search direction (the
+// after an accurate residual replacement: freeze the columns whose accurate residual meets
+// tol and count the rest.  A column whose recursive residual has run more than 100x below the
+// accurate one, or claims tol while the accurate residual does not, has a stale search direction (the
 // recursion went on past its attainable accuracy): rho = 0 makes the next beta fold
 // restart it (beta = 0), as rescaling a stale direction stalls CG.
 __global__ void k_mg_freeze(int k, const double *resid, const double *relrec, double tol, int *active, double *rho,

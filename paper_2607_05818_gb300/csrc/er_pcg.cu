@@ -416,8 +416,8 @@ static er_status poll(Workspace &w, Prof &pf, int *n_active, int *err) {
 //  FP64 form: Jacobi-PCG, each column frozen when its recursive residual meets tol.
 //  FP32 form: FP32 Jacobi-PCG on the FP32-rounded network with reliable updates: every
 //  replace_every iterations (and whenever every column's recursive residual meets tol)
-//  the FP32 correction is folded into the FP64 iterate and the FP64 residual replaces
-//  the recursive one; a column stops only when that FP64 residual meets tol.
+//  the FP32 correction is folded into the double-float iterate and the accurate residual
+//  replaces the recursive one; a column stops only when that accurate residual meets tol.
 er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts &opt) {
     if (k < 4 || (k & 3)) return fail(ER_ERR_INVALID_ARG, "k must be a positive multiple of 4");
     if (!Yt || !Z) return fail(ER_ERR_INVALID_ARG, "Yt or Z is NULL");
@@ -492,7 +492,7 @@ er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er
     auto iterate = [&](int cur, Prof *p) {
         return fp32 ? fp32_iterate(g, w, Z, tol, cur, p) : fp64_iterate(g, w, Z, tol, cur, p);
     };
-    // FP32 form: fold the correction into the FP64 iterate and substitute the FP64 residual
+    // FP32 form: fold the correction into the double-float iterate and substitute the accurate residual
     auto replace = [&](int cur) {
         fp32_accum(g, w, Z, &pf);
         fp32_residual(g, w, Yt, tol, cur, 1, &pf);
@@ -542,7 +542,7 @@ er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er
         st = poll(w, pf, &n_active, &err);
         if (st != ER_OK) return st;
         if (fp32 && n_active == 0 && last_replace != it) {
-            // every column's recursive residual meets tol: the FP64 residual decides
+            // every column's recursive residual meets tol: the accurate residual decides
             replace(cur);
             ++replacements;
             last_replace = it;
@@ -555,7 +555,7 @@ er_status solve_core(const GridDev &g, Workspace &w, const void *Yt, void *Z, er
         replace(cur);
         ++replacements;
     }
-    // final FP64 residual (record only)
+    // final accurate residual (record only)
     if (fp32) {
         fp32_residual(g, w, Yt, tol, 1 - cur, 0, &pf);
         fp32_final(g, w, Z, &pf);

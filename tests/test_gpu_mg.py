@@ -2,7 +2,7 @@
 against the oracle's same-seed JL estimate.
 
 The preconditioner changes only the path to the solution: a column still stops when its
-FP64 residual meets tol, so the maps must meet the FP32 form's bound (1e-3 relative)
+accurate (double-float) residual meets tol, so the maps must meet the FP32 form's bound (1e-3 relative)
 against the oracle on every case the Jacobi path is tested on, plus networks whose
 coarsening is uneven (odd W and H, a 1 x L chain, floating islands that must stay out of
 every aggregate).  On the precision recipe the V-cycle must cut the iteration count by a
@@ -83,7 +83,7 @@ def test_mg_cuts_iterations_and_is_deterministic(er):
     np.testing.assert_array_equal(Rm, Rm2)
     print(f"Jacobi {stj['iterations']} iterations, multigrid {stm['iterations']}")
     assert stm["iterations"] * 5 <= stj["iterations"], (stj["iterations"], stm["iterations"])
-    # both stop at the same FP64 residual, so they agree to the accuracy that tol gives
+    # both stop at the same accurate residual, so they agree to the accuracy that tol gives
     assert rel_err(Rm, Rj) <= 5e-4
 
 
