@@ -502,6 +502,23 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
         mg_tma4(sm, &mpt, &bar, g.c0, g.x0 - 1, g.y0 - 1, g.t);
         mg_tma4(sm + U_V, &mct, &bar, 0, g.x0 - 1, g.y0 - 1, g.t);
     }
+    // r (and for the x update x and p'_prev) are read straight from global memory after
+    // the stencil; ask L2 for their 128-byte row slices now, so that the DRAM reads overlap
+    // the wait for the tile's bulk copy (one thread per node row slice: column group 0)
+    if ((threadIdx.x & 7) == 0 && g.c0 < k) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int node = (threadIdx.x >> 3) + 32 * h;
+            const int xg = g.x0 + node % CX, yg = g.y0 + node / CX;
+            if (xg >= F.W || yg >= F.H) continue;
+            const int64_t o = ((int64_t)(g.t * F.H + yg) * F.W + xg) * k + g.c0;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(r + o));
+            if constexpr (XPAIR) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(x + o));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(p_prev + o));
+            }
+        }
+    }
     // the CTA's 32 step lengths, converted to FP32 once per column (an FP64 -> FP32
     // conversion runs on the FP64 pipe: one per thread and column kept it 18% busy)
     __shared__ __align__(16) float s_a[TCB], s_ap[TCB];
