@@ -31,6 +31,12 @@
  *  - Errors are returned as er_status; nothing is thrown across the ABI.  Invalid
  *    arguments are rejected on the host before any launch.  er_last_error()
  *    returns a thread-local message for the last failing call of this thread.
+ *  - Threads: calls on different grids may run concurrently from different host threads
+ *    (each grid's solve workspace, hierarchy and scratch are its own).  Calls that use a
+ *    grid's cached workspace (er_solve, er_pair_reff, er_ir_drop) are serialised per grid
+ *    by a lock; er_sketch and er_reff_map only read the grid.  er_grid_destroy must not
+ *    overlap other calls on the same grid.  er_solve_noalloc is the exception (one
+ *    process-wide scratch array; see there).
  */
 #ifndef ER_H
 #define ER_H
