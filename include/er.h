@@ -217,13 +217,14 @@ er_status er_solve_noalloc(er_grid *g, const void *Yt, void *Z, int32_t k, const
 typedef struct {
     int32_t n_grids;
     int32_t iterations;       /* iterations of the batch (the slowest network) */
-    int32_t replacements;     /* accurate residual replacements */
+    int32_t replacements;     /* accurate residual replacements (multigrid mode: the most of any network) */
     int32_t converged;        /* networks whose every column met tol */
     int64_t nodes;            /* non-floating nodes over all networks */
     double max_rel_residual;  /* final accurate residual, max over all networks and columns */
     double seconds;           /* host wall time of the call */
     int32_t launches;         /* kernels launched */
-    int32_t graph_captures;   /* CUDA graphs captured (one per change of the work list) */
+    int32_t graph_captures;   /* CUDA graphs captured (one per change of the work list; 0 in the
+                                 multigrid mode, whose solves capture their own graphs) */
 } er_batch_stats;
 
 /* Batching form: the all-node R maps of n networks (e.g. TSV-placement candidates of
