@@ -87,6 +87,8 @@ def block_loads(inst, current_per_block=1.0):
 def bump_share(currents, share=0.95):
     """Fraction of bumps that together carry `share` of the total current, largest first."""
     mag = np.abs(np.asarray(currents, dtype=np.float64))
+    if not mag.sum() > 0:
+        return 0.0  # no current: no bump is needed to carry any share of it
     need = share * mag.sum() * (1 - 1e-12)
     acc, used = 0.0, 0
     for c in sorted(mag, reverse=True):
