@@ -1,7 +1,8 @@
 """Benchmark: all-node effective-resistance map throughput (nodes/s) on one GB300 per rank.
 
 One step = the whole hot path on one synthetic network already resident in HBM:
-JL sketch (er_sketch) + k-RHS Jacobi-PCG solve (er_solve) + R map (er_reff_map).
+JL sketch (er_sketch) + k-RHS preconditioned CG solve (er_solve; multigrid V-cycle by
+default) + R map (er_reff_map).
 Default workload: 4 tiers x 512x512 (1,048,576 nodes), k = 256, the FP32 form: FP32
 vectors and stencil, double-float dot sums, a double-float iterate (pairs of FP32 numbers)
 with the accurate residual substituted every 50 iterations (reliable updates), stopped at an
@@ -47,11 +48,18 @@ def parse():
     p.add_argument("--precond", default="mg", choices=["jacobi", "mg"],
                    help="FP32 form: Jacobi or aggregation-multigrid V-cycle preconditioner")
     p.add_argument("--k", type=int, default=256)
+    p.add_argument("--shard", default="replicas", choices=["replicas", "columns"],
+                   help="N > 1: every rank maps its own network (replicas, weak scaling), or all ranks map "
+                        "one network, each solving its share of the sketch columns, and the partial maps are "
+                        "summed (columns, strong scaling)")
     p.add_argument("--tol", type=float, default=None)
     p.add_argument("--no-accuracy", action="store_true")
+    p.add_argument("--acc-block", type=int, default=0,
+                   help="solve the plain FP64 reference in blocks of this many sketch columns (0: all at once)")
     p.add_argument("--cpu-sample", type=int, default=256, help="W=H of the oracle's bounded sample")
     p.add_argument("--batch-count", type=int, default=512, help="candidates of the batching workload")
-    p.add_argument("--autotune", action="store_true", help="batching workload: autotuned tile rows")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="batching workload: library default tile rows instead of the autotuner's per size class")
     p.add_argument("--sur-train", type=int, default=1024, help="surrogate workload: solver-labelled training configs")
     p.add_argument("--sur-screen", type=int, default=4096, help="surrogate workload: screened candidates")
     p.add_argument("--sur-k", type=int, default=64, help="surrogate workload: JL columns of labels and verification")
@@ -77,28 +85,85 @@ def cpu_sample_instance(W):
     return I.precision_4x512(W=W, H=W, n_tsv=max(1, int(round(2000 * f))), n_clusters=max(1, int(round(40 * f))))
 
 
-def oracle_step(inst, k, seed):
-    """The CPU oracle as it stands: sparse factorisation, sketch, k-RHS solves, row norms."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_step(inst, k, seed, threads=None):
+    """The CPU oracle as it stands, phase by phase: assembly and sparse LU factorisation of G
+    (SuperLU, one thread), the C sketch, the k right-hand-side solves in column blocks of 8 on
+    `threads` host threads, and the row norms.  Returns (seconds per phase, non-floating nodes,
+    threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     from oracle import exact
     from oracle import sketch as osk
+    threads = threads or os.cpu_count() or 1
+    ph = {}
     t0 = time.perf_counter()
     f = exact.SparseFactor(inst)
+    ph["factor_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     Yt = osk.sketch(inst, k, seed)
-    Z = f.solve(Yt)
-    R = np.sum(Z * Z, axis=1)
+    ph["sketch_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    blocks = list(range(0, k, 8))
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda j: f.solve(Yt[:, j:j + 8]), blocks))
+    ph["solves_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R = sum(np.sum(Z * Z, axis=1) for Z in parts)
     R[f.floating] = np.inf
-    return time.perf_counter() - t0, int(np.sum(~f.floating))
+    ph["row_norms_s"] = time.perf_counter() - t0
+    ph["total_s"] = sum(ph.values())
+    return ph, int(np.sum(~f.floating)), threads
 
 
 def cpu_baseline(args):
+    """The oracle timed on the host cores on two bounded samples of the bench recipe (4 tiers of
+    128^2 and 256^2), phases separately; the 4 x 512^2 figure is extrapolated from the measured
+    growth of each phase between the two samples (labelled as such)."""
     from oracle import build as ob
     ob.build()
-    inst = cpu_sample_instance(args.cpu_sample)
-    dt, n_ok = oracle_step(inst, args.k, inst.meta.get("seed", 1))
-    return {"value": n_ok / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one {inst.T}x{inst.W}x{inst.H} network ({inst.n} nodes) of the same recipe, k={args.k}: "
-                      f"SuperLU factorisation + C sketch + {args.k} sparse solves + row norms, "
-                      f"single-threaded, {dt:.1f} s"}
+    res = {}
+    for W in (args.cpu_sample // 2, args.cpu_sample):
+        inst = cpu_sample_instance(W)
+        ph, n_ok, thr = oracle_step(inst, args.k, inst.meta.get("seed", 1))
+        res[W] = (ph, n_ok, inst)
+    (ph_s, n_s, _), (ph_l, n_l, inst_l) = res[args.cpu_sample // 2], res[args.cpu_sample]
+    n_bench = 4 * 512 * 512
+    est = 0.0
+    growth = {}
+    for key in ("factor_s", "sketch_s", "solves_s", "row_norms_s"):
+        a = np.log(max(ph_l[key], 1e-9) / max(ph_s[key], 1e-9)) / np.log(n_l / n_s)
+        growth[key] = float(a)
+        est += ph_l[key] * (n_bench / n_l) ** max(a, 1.0)
+    return {"value": n_l / ph_l["total_s"], "unit": UNIT, "cores": thr, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"one {inst_l.T}x{inst_l.W}x{inst_l.H} network ({inst_l.n} nodes) of the bench recipe, k={args.k}: "
+                      f"SuperLU factorisation (1 thread), C sketch, {args.k} sparse solves in blocks of 8 on {thr} "
+                      f"threads, row norms",
+            "phases_s": {k_: round(v, 3) for k_, v in ph_l.items()},
+            "phases_s_smaller_sample": {k_: round(v, 3) for k_, v in ph_s.items()},
+            "same_config": False,
+            "extrapolated_bench_network": {
+                "value": n_bench / est, "unit": UNIT, "seconds": est,
+                "note": "4x512x512: each phase scaled from the 256^2 sample by its measured growth exponent "
+                        "between the 128^2 and 256^2 samples (at least linear)", "growth_exponents": growth}}
 
 
 class ClockSampler:
@@ -165,6 +230,16 @@ def combine_ranks(units, seconds, world, device="cpu"):
     return float(n.item()), float(t.item())
 
 
+def reduce_partial_map(R, world):
+    """Column sharding: R_i = sum_j Z_ij^2 runs over independent sketch columns, so the map of the
+    whole sketch is the sum of the ranks' partial maps over their column shards.  One sum
+    all-reduce of the n-vector (in place; NCCL on GPUs, gloo on CPU) is the only exchange."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(R, op=dist.ReduceOp.SUM)
+    return R
+
+
 def load_peaks():
     """Measured HBM and BF16 peaks of this GPU model, else the stated fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -207,7 +282,7 @@ def ncu_traffic(kernel, workload):
 
 def run_batch(args, rank, world, local_rank):
     """Batching form: 512 TSV-placement candidates (k = 64) through er_batch_solve, with the
-    multigrid preconditioner (concurrent per-network solves; the default, --precond mg) or
+    multigrid preconditioner (one CUDA graph of all networks' solves; the default, --precond mg) or
     Jacobi (shared launches), the other mode timed once beside it, against the same
     candidates solved one after another (er_solve per candidate, warm workspace)."""
     import torch
@@ -230,9 +305,12 @@ def run_batch(args, rank, world, local_rank):
     use_mg = args.precond == "mg"
     opts_run, opts_other = (opts_mg, opts) if use_mg else (opts, opts_mg)
     rows = None
-    if args.autotune:
+    t_tune = 0.0
+    if not args.no_autotune:  # per size class (tiers, W, H), measured once, outside the timed region
         from paper_2607_05818_gb300 import autotune
-        rows = [autotune.best_rows(c, k) for c in cands]
+        tt = time.perf_counter()
+        rows = [autotune.best_mg_rows(c, k) if use_mg else autotune.best_rows(c, k) for c in cands]
+        t_tune = time.perf_counter() - tt
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         er.batch_solve(grids, k, 1, R, opts=opts_run, tile_rows=rows)
@@ -294,11 +372,13 @@ def run_batch(args, rank, world, local_rank):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"batch_candidates_{len(cands)}", "k": k, "candidates": len(cands),
                    "nodes": n_ok, "iterations": last["iterations"], "converged": last["converged"],
-                   "graph_captures": last["graph_captures"], "tile_rows": "autotuned" if rows else "default 64",
+                   "graph_captures": last["graph_captures"],
+                   "tile_rows": (f"autotuned per size class ({len(set(rows))} distinct choices, "
+                                 f"{t_tune:.1f} s to tune, untimed)" if rows else "library default"),
                    "max_rel_residual": last["max_rel_residual"],
-                   "mode": "multigrid: concurrent per-network solves on 8 worker streams" if use_mg
-                   else "Jacobi: shared launches over a (network, tile) work list"},
-        "other_mode": {"mode": "Jacobi shared launches" if use_mg else "multigrid concurrent solves",
+                   "mode": "multigrid: one CUDA graph, each network's loop a device-side conditional node"
+                   if use_mg else "Jacobi: shared launches over a (network, tile) work list"},
+        "other_mode": {"mode": "Jacobi shared launches" if use_mg else "multigrid graph of all networks",
                        "value": n_ok / other_s, "unit": UNIT, "seconds": other_s,
                        "iterations": st_other["iterations"], "converged": st_other["converged"],
                        "note": "one er_batch_solve call, host wall time"},
@@ -775,14 +855,68 @@ def run_planning(args, rank, world, local_rank):
     }
 
 
+def fp64_accuracy(er, g, inst, k, seed, R, tol32, block, dev, fp32_solve_s):
+    """This form's R map against plain FP64 GPU PCG (tol 1e-12) on the same network and seed,
+    outside the timed region.  With block > 0 the FP64 reference solves the k sketch columns in
+    blocks of `block` (the columns are independent solves; each block's partial map is summed),
+    which bounds its memory on the large networks.  Also plain FP64 stopped at this form's
+    tolerance, for the speedup at equal accuracy (in block mode measured on the first block and
+    scaled to k columns)."""
+    import torch
+    block = k if block <= 0 or block >= k else block
+    Y64 = torch.empty((inst.n, k), dtype=torch.float64, device=dev)
+    er.sketch(g, k, seed, "fp64", Y64)
+    R64 = torch.zeros(inst.n, dtype=torch.float64, device=dev)
+    Rb = torch.empty_like(R64)
+    Zb = torch.empty((inst.n, block), dtype=torch.float64, device=dev)
+    its, secs, same = [], 0.0, None
+    for b0 in range(0, k, block):
+        Yb = Y64 if block == k else Y64[:, b0:b0 + block].contiguous()
+        _, st = er.solve(g, Yb, Zb, block, "fp64")
+        er.reff_map(g, Zb, block, "fp64", Rb)
+        R64 += Rb
+        its.append(st["iterations"])
+        secs += st["seconds"]
+        if b0 == 0:  # plain FP64 PCG stopped at the same residual tolerance as this form
+            o_same = er.default_solve_opts("fp64")
+            o_same.tol = tol32
+            Zs = torch.empty_like(Zb)
+            _, st_same = er.solve(g, Yb, Zs, block, "fp64", o_same)
+            Rs = torch.empty_like(R64)
+            er.reff_map(g, Zs, block, "fp64", Rs)
+            same = (st_same, Rs.cpu().numpy(), Rb.cpu().numpy())
+            del Zs, Rs
+        del Yb
+    torch.cuda.synchronize()
+    a, b = R.cpu().numpy(), R64.cpu().numpy()
+    fin = np.isfinite(b)
+    assert np.array_equal(np.isfinite(a), fin)
+    rel = np.abs(a[fin] / b[fin] - 1)
+    st_same, rs, rb = same
+    rel_same = np.abs(rs[fin] / rb[fin] - 1)
+    same_s = st_same["seconds"] * (k / block)
+    return {"vs": "plain FP64 GPU PCG (Jacobi, tol 1e-12), same network and seed", "max_rel_err": float(rel.max()),
+            "mean_rel_err": float(rel.mean()), "nodes_compared": int(fin.sum()), "tol": tol32,
+            "fp64_ref_iterations": max(its), "fp64_ref_solve_s": secs,
+            "fp64_ref_column_blocks": k // block,
+            "fp64_same_tol": {"iterations": st_same["iterations"], "solve_s": same_s,
+                              "max_rel_err": float(rel_same.max()),
+                              "note": "all columns" if block == k else
+                              f"measured on the first {block} columns (vs the reference's same columns), "
+                              f"time scaled to {k}"},
+            "this_form_solve_s": fp32_solve_s, "speedup_vs_fp64_same_tol": same_s / fp32_solve_s}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2607_05818_gb300 import er
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    inst = make_workload(args.workload, rank)
-    k = args.k
+    shard = args.shard == "columns" and world > 1
+    inst = make_workload(args.workload, 0 if shard else rank)  # column shards: one network on every rank
+    k_total = args.k
+    j0, k = er.column_shard(k_total, world, rank) if shard else (0, k_total)
     seed = int(inst.meta.get("seed", 1))
     prec = args.prec
     dt = torch.float32 if prec == "fp32" else torch.float64
@@ -804,9 +938,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     def step():
-        er.sketch(g, k, seed, prec, Yt)
+        if shard:
+            er.sketch_cols(g, k_total, j0, k, seed, prec, Yt)
+        else:
+            er.sketch(g, k, seed, prec, Yt)
         _, st = er.solve(g, Yt, Z, k, prec, opts)
         er.reff_map(g, Z, k, prec, R)
+        if shard:
+            reduce_partial_map(R, world)
         return st
 
     for _ in range(args.warmup):
@@ -828,7 +967,8 @@ def run_ours(args, rank, world, local_rank):
             stats.append(step())
         e1.record(stream)
         barrier()
-    n_total, s_max = combine_ranks(n_ok, e0.elapsed_time(e1) / 1e3, world, dev)
+    # replicas: every rank's network counts; column shards: the one network all ranks mapped
+    n_total, s_max = combine_ranks(n_ok if (not shard or rank == 0) else 0, e0.elapsed_time(e1) / 1e3, world, dev)
     ms = 1e3 * s_max
     value = n_total * args.steps / s_max
 
@@ -850,7 +990,7 @@ def run_ours(args, rank, world, local_rank):
         kinds = [(1, "k_mg_upd_tile<true>", 6 * nk * es + coef),    # p', r, x, p'_prev in; r, x out
                  (4, "k_mg_upd_tile<false>", 3 * nk * es + coef),   # p', r in; r out
                  (0, "k_mg_dir_tile", 3 * nk * es + coef),          # z, p in; p' out
-                 (7, "k_mg_tile<true, true> (finest level)", int(2.25 * nk * es) + coef),
+                 (7, "k_mg_sweep<true> (finest level)", int(2.25 * nk * es) + coef),
                  (6, "k_mg_tile<false, false> (finest level)", int(1.25 * nk * es) + coef),
                  (5, "V-cycle on the coarse levels", int(3.5 * nk * es / 3)),
                  (2, "k_tma<MODE_R> (double-float residual)", 4 * nk * es + coef)]  # x {hi, lo}, b in; r out
@@ -890,34 +1030,8 @@ def run_ours(args, rank, world, local_rank):
               "max_rel_residual": max(s["max_rel_residual"] for s in stats)}
     acc = None
     if rank == 0 and not args.no_accuracy and prec == "fp32":
-        # accuracy of this form against plain FP64 on the same network and seed (outside timing)
-        Y64 = torch.empty((inst.n, k), dtype=torch.float64, device=dev)
-        Z64 = torch.empty_like(Y64)
-        R64 = torch.empty_like(R)
-        er.sketch(g, k, seed, "fp64", Y64)
-        _, st64 = er.solve(g, Y64, Z64, k, "fp64")
-        er.reff_map(g, Z64, k, "fp64", R64)
-        torch.cuda.synchronize()
-        a, b = R.cpu().numpy(), R64.cpu().numpy()
-        fin = np.isfinite(b)
-        rel = np.abs(a[fin] / b[fin] - 1)
-        # plain FP64 PCG stopped at the same residual tolerance as this form: the speedup at equal accuracy
-        o_same = er.default_solve_opts("fp64")
-        o_same.tol = opts.tol
-        _, st_same = er.solve(g, Y64, Z64, k, "fp64", o_same)
-        er.reff_map(g, Z64, k, "fp64", R64)
-        torch.cuda.synchronize()
-        c = R64.cpu().numpy()
-        rel_same = np.abs(c[fin] / b[fin] - 1)
-        fp32_solve_s = float(np.median([s["seconds"] for s in stats]))
-        acc = {"vs": "plain FP64 GPU PCG (tol 1e-12), same network and seed", "max_rel_err": float(rel.max()),
-               "mean_rel_err": float(rel.mean()), "tol": opts.tol,
-               "fp64_ref_iterations": st64["iterations"], "fp64_ref_solve_s": st64["seconds"],
-               "fp64_same_tol": {"iterations": st_same["iterations"], "solve_s": st_same["seconds"],
-                                 "max_rel_err": float(rel_same.max())},
-               "this_form_solve_s": fp32_solve_s,
-               "speedup_vs_fp64_same_tol": st_same["seconds"] / fp32_solve_s}
-        del Y64, Z64, R64
+        acc = fp64_accuracy(er, g, inst, k_total, seed, R, opts.tol, args.acc_block, dev,
+                            float(np.median([s["seconds"] for s in stats])))
     # end to end through the host entry point: host arrays in, host R out (copies inside)
     e2e = None
     if rank == 0:
@@ -928,7 +1042,7 @@ def run_ours(args, rank, world, local_rank):
             opts_e.tol = opts.tol
         R_host = np.empty(inst.n)
         t0 = time.perf_counter()
-        er.reff_map_host(inst, k, seed, prec, opts_e, R_host)
+        er.reff_map_host(inst, k_total, seed, prec, opts_e, R_host)
         e2e_s = time.perf_counter() - t0
         e2e = {"value": n_ok / e2e_s, "unit": UNIT, "h2d_bytes_per_step": info["h2d_bytes"],
                "d2h_bytes_per_step": inst.n * 8, "seconds": e2e_s,
@@ -951,11 +1065,12 @@ def main():
         inst = cpu_sample_instance(args.cpu_sample)
         for _ in range(args.warmup):
             oracle_step(inst, args.k, 1)
-        ts = []
-        n_ok = 0
+        ts, phases = [], []
+        n_ok, thr = 0, 1
         for _ in range(args.steps):
-            dt, n_ok = oracle_step(inst, args.k, 1)
-            ts.append(dt)
+            ph, n_ok, thr = oracle_step(inst, args.k, 1)
+            ts.append(ph["total_s"])
+            phases.append(ph)
         tot = sum(ts)
         v = n_ok * args.steps / tot
         print(json.dumps({
@@ -964,8 +1079,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "k": args.k,
                                             "sample": f"{inst.T}x{inst.W}x{inst.H}"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one {inst.T}x{inst.W}x{inst.H} network of the same recipe per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "cpu_model": cpu_model(),
+                             "nproc": os.cpu_count(),
+                             "sample": f"one {inst.T}x{inst.W}x{inst.H} network of the same recipe per step "
+                                       f"(SuperLU factorisation, C sketch, {args.k} solves on {thr} threads, row norms)",
+                             "phases_s_last_step": {k_: round(v_, 3) for k_, v_ in phases[-1].items()} if phases else None},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
@@ -986,17 +1104,23 @@ def main():
     value, ms, result, rl, launches, clocks, acc, e2e, n_total = run_ours(args, rank, world, local_rank)
     if rank == 0:
         cpu = cpu_baseline(args) if world == 1 else None
+        sharded = args.shard == "columns" and world > 1
+        n_rank = n_total if sharded else int(n_total / world)  # nodes each rank's arrays hold
+        k_rank = args.k // world if sharded else args.k
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if (args.shard == "columns" and world > 1) else "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "k": args.k, "precision": args.prec,
-                       "nodes_per_rank": int(n_total / world),
+                       "nodes_per_rank": n_rank,
+                       "parallelism": (f"column shards: one network, {args.k} sketch columns split over {world} ranks, "
+                                       f"partial maps summed by one all-reduce" if args.shard == "columns" and world > 1
+                                       else f"replicas: {world} independent network(s), no collective on the data path"),
                        "preconditioner": "aggregation multigrid V-cycle" if (args.precond == "mg" and args.prec == "fp32")
                        else "Jacobi",
                        "l2": f"inputs larger than L2 (each [n][k] array is "
-                             f"{int(n_total / world) * args.k * (4 if args.prec == 'fp32' else 8) / 2**30:.2f} GiB)",
+                             f"{n_rank * k_rank * (4 if args.prec == 'fp32' else 8) / 2**30:.2f} GiB)",
                        "iterations_per_step": result["rank0_iterations"],
                        "fp64_residual_replacements_per_step": result["replacements"],
                        "tol": args.tol if args.tol is not None else ("1e-7" if args.prec == "fp32" else "1e-12"),

@@ -12,7 +12,8 @@
  *
  * The all-node map is computed as
  *   Y^T = M^T Q^T            (er_sketch; M = [W^{1/2} B; D^{1/2}], Q Rademacher)
- *   Z   = G^-1 Y^T           (er_solve; k right-hand sides, Jacobi-PCG)
+ *   Z   = G^-1 Y^T           (er_solve; k right-hand sides, preconditioned CG: Jacobi, or
+ *                             one aggregation-multigrid V-cycle per iteration)
  *   R_i = ||Z_i||^2          (er_reff_map)
  * The sketch and the CG solve are not in the paper (it uses a reduced TSV system
  * for bump-load pairs, Sec. III-C/D); they reach the Eq. 2 quantity for all
@@ -61,8 +62,8 @@ typedef enum {
 
 typedef enum {
     ER_FP64 = 0,        /* FP64 storage and arithmetic throughout */
-    ER_FP32_REFINE = 1  /* FP32 storage/stencil/updates, FP64-accurate dot products,
-                           FP64 true-residual replacement and restart sweeps */
+    ER_FP32_REFINE = 1  /* FP32 storage/stencil/updates; dot sums, iterate and the periodic
+                           true-residual replacement in double-float (FP64-class accuracy) */
 } er_precision;
 
 /* One tier: a W x H mesh.  gx[y*(W-1) + x] is the conductance (siemens) of segment
@@ -105,7 +106,11 @@ typedef struct {
     int32_t use_graph;     /* 1: replay each poll period from a captured CUDA graph */
     int32_t profile;       /* 1: time every pass with CUDA events on the solver's stream
                               (disables graphs); fills er_solve_stats.kernel_ms */
-    int32_t tile_rows;     /* y rows swept by one CTA (0 = default 64; clipped to H) */
+    int32_t tile_rows;     /* Jacobi: y rows swept by one CTA of the stencil passes (0 = default
+                              64; clipped to H).  Multigrid: rows per CTA of the finest level's
+                              prolongation (rounded down to a multiple of 8; 0 = automatic); its
+                              dot partials are kept per 8-row group, so this changes the speed,
+                              not the result */
     int32_t block_order;   /* 0 default, 1 RHS column blocks of a tile adjacent in launch
                               order, 2 column blocks outermost */
     int32_t precond;       /* 0 Jacobi (D^-1); 1 aggregation multigrid: one V-cycle per
@@ -170,9 +175,18 @@ er_status er_grid_info(const er_grid *g, int64_t *n_nodes, int64_t *n_floating,
 er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt,
                     void *stream);
 
+/* Columns j0 .. j0 + k_local - 1 of the k_total-column sketch of er_sketch (the same Q[j][e],
+ * scale 1/sqrt(k_total)) into device array Yt [n][k_local]: one column shard of the sketch.
+ * Since R_i = sum_j Z_ij^2 runs over independent columns, shards solved separately (one per
+ * GPU, say) give partial maps whose sum is the map of the whole sketch.  k_local is a positive
+ * multiple of 4, 0 <= j0 and j0 + k_local <= k_total.  Async on `stream`. */
+er_status er_sketch_cols(er_grid *g, int32_t k_total, int32_t j0, int32_t k_local, uint64_t seed, er_precision prec,
+                         void *Yt, void *stream);
+
 /* Solve G Z = Yt for k right-hand sides (device arrays [n][k], Z written).
- * Jacobi-preconditioned CG from X0 = 0; a column stops when its Jacobi-weighted
- * residual ||r||_{D^-1} / ||b||_{D^-1} meets opts->tol and is then frozen.
+ * Preconditioned CG from X0 = 0 (Jacobi, or with precond = 1 one multigrid V-cycle per
+ * iteration; see below); a column stops when its Jacobi-weighted residual
+ * ||r||_{D^-1} / ||b||_{D^-1} meets opts->tol and is then frozen.
  * ER_FP64: FP64 throughout (run as CG on D^-1/2 G D^-1/2, identical iterates).
  * ER_FP32_REFINE: FP32 vectors, stencil and updates on the network with every
  * conductance rounded to FP32 once (which moves any R by at most a relative 2^-24);
@@ -186,12 +200,13 @@ er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, voi
  * precond = 1 (FP32 form): the preconditioner is one V-cycle of an aggregation multigrid
  * instead of D^-1.  Level l+1 aggregates 2 x 2 nodes of every tier of level l; since the
  * Galerkin product P^T G P of a network's matrix is again a network (segments between
- * aggregates kept, those inside dropped, TSVs and pads moved to their aggregate), every
- * level is a grid built like er_grid_create's, down to at most 8 x 8 nodes per tier; one
- * damped-Jacobi sweep before and after the coarse correction, damped-Jacobi sweeps on the
- * coarsest level (a fixed symmetric operator, as CG needs).  The hierarchy is built on the
- * first such call and cached on the grid.  A grid of at most 8 x 8 nodes per tier and 2,048
- * nodes uses Jacobi.  The library allocates (and caches on the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at
+ * aggregates kept, those inside dropped, parallel TSVs and pads of an aggregate merged into
+ * one), every level is a grid built like er_grid_create's.  Coarsening stops at the first
+ * level of at most 512 nodes, which is solved exactly by its dense inverse (FP64 Cholesky on
+ * the host, stored in FP32); one damped-Jacobi sweep (weight 0.8) runs before and after each
+ * coarse correction, so the cycle is a fixed symmetric positive definite operator, as CG
+ * needs.  The hierarchy is built on the first such call and cached on the grid.  A grid that
+ * does not coarsen to at most 2,048 nodes (too many tiers) returns ER_ERR_INVALID_ARG.  The library allocates (and caches on the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at
  * maxit (Z valid, stats filled), ER_ERR_TIMEOUT if a kernel's bounded wait expired.
  * Synchronises. */
 er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec,
@@ -202,15 +217,17 @@ er_status er_solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision 
  * device allocation after start-up, memory-capped serving processes that must not grow,
  * or loops that cannot accept the implicit synchronisation of cudaMalloc/cudaFree.
  * (The paper has no counterpart: this is a deployment variant of the solve.)
- * The solver workspace lives in one file-scope device array of about 9.1 MB, held by
- * every GPU that loads the library until the process exits; sizes are limited to
- * n*k <= 262144 and k <= 4096, and larger requests return ER_ERR_INVALID_ARG.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress) and should
- * come before any stream capture.  All calls share the array: each call clears the
- * counters and flags it needs, runs on `stream` without graphs or event timing, and
- * returns when done; calls are serialised by a process-wide lock, and calls that overlap
- * on the GPU would race.  Yt and Z are FP64 [n][k] device arrays as for er_solve; the
- * grid must have been created beforehand.  Same statuses as er_solve. */
+ * The solver workspace lives in one file-scope device array of about 9.1 MB; sizes are
+ * limited to n*k <= 262144 and k <= 4096, and larger requests return ER_ERR_INVALID_ARG.
+ * er_grid_create looks up the array's device address on its device (cudaGetSymbolAddress,
+ * which loads the library module that holds the array and commits its 9.1 MB): every GPU on
+ * which a grid was created holds the array until the process exits, and a call of
+ * er_solve_noalloc neither loads a module nor commits memory.  All calls share the array:
+ * each call clears the counters and flags it needs, runs on `stream` without graphs or
+ * event timing, and returns when done (after an error, once the stream has drained); calls
+ * are serialised by a process-wide lock, and calls that overlap on the GPU would race.  Yt
+ * and Z are FP64 [n][k] device arrays as for er_solve; the grid must have been created
+ * beforehand.  Same statuses as er_solve. */
 er_status er_solve_noalloc(er_grid *g, const void *Yt, void *Z, int32_t k, const er_solve_opts *opts,
                            er_solve_stats *stats, void *stream);
 
@@ -236,12 +253,20 @@ typedef struct {
  *     graph per poll period; networks leave the work list as they converge.  tile_rows[c]
  *     (nullable) overrides the y rows swept per CTA for network c (the autotuner's choice).
  *     Workspace is allocated for the call and freed before it returns.
- *   opts->precond == 1 (multigrid): each network runs er_sketch + er_solve (multigrid
- *     V-cycle) + er_reff_map exactly as alone, on up to 8 host worker threads with one
- *     stream each, largest networks first, so small networks overlap on the GPU.  Each
- *     grid keeps its solve workspace and hierarchy cached (as after er_solve); a grid may
- *     appear only once (ER_ERR_INVALID_ARG otherwise); tile_rows is ignored.  On a hard
- *     error the remaining networks are skipped and the first error is returned. */
+ *   opts->precond == 1 (multigrid): every network's er_sketch + er_solve (multigrid V-cycle)
+ *     + er_reff_map, with exactly those kernels, is one branch of a single CUDA graph launched
+ *     once, so the launches of all networks interleave on the GPU with no host polling: each
+ *     branch's iteration loop is a device-side conditional (WHILE) node whose control kernel
+ *     ends it when the network's columns meet tol (the accurate residual replacement runs under
+ *     a nested IF node exactly when er_solve's host loop would run it), so converged networks
+ *     leave the GPU while the others continue.  Each map equals the single-network map
+ *     bitwise.  Every network needs more than 512 nodes and a tier wider than one node; a
+ *     grid may appear only once (ER_ERR_INVALID_ARG otherwise).  tile_rows[c] (nullable; 0 =
+ *     automatic) sets the rows per CTA of network c's finest-level prolongation (the
+ *     autotuner's choice; rounded down to a multiple of 8; it changes the speed, not the
+ *     result).  Each grid keeps its solve workspace and hierarchy cached (as after er_solve);
+ *     the sketch and Z arrays of all networks are allocated for the call and freed before it
+ *     returns. */
 er_status er_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, er_precision prec,
                          const int32_t *tile_rows, double *const *R_out, const er_solve_opts *opts,
                          er_batch_stats *stats, void *stream);
@@ -286,6 +311,53 @@ er_status er_surrogate_grad(er_surrogate *s, const void *maps, const float *targ
 /* er_surrogate_grad followed by one Adam step (beta 0.9/0.999, eps 1e-8) at rate lr. */
 er_status er_surrogate_train_step(er_surrogate *s, const void *maps, const float *target, const uint8_t *mask,
                                   int32_t B, float lr, double *loss, void *stream);
+
+/* Requested output-channel tile width (N of the tcgen05 MMA) of the surrogate's 3x3
+ * convolutions: 0 (the default) lets the library choose per layer (the widest of 256, 192,
+ * 128, 96, 64, 32 that divides the layer's channels and still gives every SM a tile); 32, 64,
+ * 96, 128, 192 or 256 is used on every layer whose output channels it divides.  The
+ * arithmetic does not depend on the width.  ER_ERR_INVALID_ARG for other values. */
+er_status er_surrogate_set_tile_n(er_surrogate *s, int32_t tile_n);
+
+/* ---- the surrogate's 3x3 convolution layers, one at a time ---------------------------- */
+
+/* What one convolution launch ran. */
+typedef struct {
+    int32_t kernel;   /* 1: persistent TMA kernel (128-pixel boxes); 2: cp.async-staged kernel */
+    int32_t tile_n;   /* output channels per tile (N of the tcgen05 MMA) */
+    int32_t k_step;   /* input channels per K step (32 or 64) */
+    int32_t reserved;
+} er_conv_info;
+
+/* y = act(bias + conv3x3(x, w)) with zero padding: y[b][h][w][o] = bias[o] +
+ * sum_{ky,kx,c} x[b][h+ky-1][w+kx-1][c] w[o][ky][kx][c], then ReLU if relu != 0; the layer of
+ * er_surrogate_* on its own.  x [B][H][W][cin] and y [B][H][W][cout] are BF16 device arrays,
+ * w [cout][3][3][cin] and bias [cout] (nullable) FP32 device arrays; w is rounded to BF16,
+ * products are accumulated in FP32 in tensor memory on the tcgen05 tensor cores and y is
+ * rounded to BF16.  cin and cout are positive multiples of 32; tile_n as for
+ * er_surrogate_set_tile_n.  info (host, nullable) receives what ran.  The BF16 weight copies
+ * are allocated and freed in stream order; synchronises `stream`; ER_ERR_TIMEOUT if a
+ * bounded wait expired. */
+er_status er_conv3x3_forward(const void *x, const float *w, const float *bias, int32_t B, int32_t H, int32_t W,
+                             int32_t cin, int32_t cout, int32_t relu, int32_t tile_n, void *y, er_conv_info *info,
+                             void *stream);
+/* Data gradient of that layer through the ReLU of its input: dx[b][h][w][c] = [x > 0] *
+ * sum_{ky,kx,o} dy[b][h-ky+1][w-kx+1][o] w[o][ky][kx][c] (zero outside the image).  dy
+ * [B][H][W][cout], x [B][H][W][cin] (the forward input) and dx [B][H][W][cin] are BF16 device
+ * arrays; w as for er_conv3x3_forward.  Runs the forward kernels on the flipped, transposed
+ * weights.  Same rules as er_conv3x3_forward. */
+er_status er_conv3x3_dgrad(const void *dy, const float *w, const void *x, int32_t B, int32_t H, int32_t W,
+                           int32_t cin, int32_t cout, int32_t tile_n, void *dx, er_conv_info *info, void *stream);
+/* Weight gradient of that layer: dw[o][ky][kx][c] = sum_{b,h,w} dy[b][h][w][o]
+ * x[b][h+ky-1][w+kx-1][c] (zero padding), FP32 [cout][3][3][cin] device array, overwritten.
+ * x and dy are BF16 device arrays as above; products accumulate in FP32.  Synchronises. */
+er_status er_conv3x3_wgrad(const void *x, const void *dy, int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                           float *dw, void *stream);
+/* Launches of the convolution kernels in this process since the last reset (host counters):
+ * [0..5] persistent TMA kernel with 32-channel K steps and N tiles of 32, 64, 96, 128, 192,
+ * 256; [6..11] the same with 64-channel K steps; [12] cp.async-staged kernel; [13] weight
+ * gradient; [14..15] zero.  The first min(n, 16) are written to counts; reset != 0 zeroes them. */
+er_status er_conv_launch_counts(int64_t *counts, int32_t n, int32_t reset);
 
 /* R_i = sum_j Z_ij^2 into device array R [n] (FP64); +inf for floating nodes.
  * Z is FP64 or FP32 per `prec`.  Async on `stream`. */

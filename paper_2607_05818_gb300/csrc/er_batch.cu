@@ -1,5 +1,6 @@
 // Batching form: the all-node R map of many uneven networks, in shared launches
-// (Jacobi, precond 0; below) or as concurrent multigrid solves (precond 1; batch_solve_mg).
+// (Jacobi, precond 0; below) or as one CUDA graph of multigrid solves (precond 1;
+// mg_batch_graph in er_mg.cu).
 //
 // Every network keeps its own grid (coefficients, TSV CSR), its own vectors and its own
 // per-column CG scalars, but each pass (A, B/B0, accurate residual, initialisation,
@@ -23,10 +24,6 @@
 
 namespace er {
 
-er_status sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt, cudaStream_t s);
-er_status reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R, cudaStream_t s);
-er_status solve(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts *opts,
-                er_solve_stats *stats, cudaStream_t s);
 
 namespace {
 
@@ -40,118 +37,6 @@ struct DevBuf {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
-
-// Multigrid batching (precond = 1).  The V-cycle has no work-list kernels, so each network
-// runs er_solve's multigrid form; kMgWorkers host threads, each with its own stream and its
-// own Yt and Z scratch (sized for the largest network), take the networks largest first, so
-// the launch-bound passes of the small networks overlap on the GPU instead of running one
-// network at a time.  Each network's sketch (seed + c), solve and map are exactly those of
-// er_sketch + er_solve + er_reff_map on that network alone.
-constexpr int kMgWorkers = 8;
-
-static er_status batch_solve_mg(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, double *const *R_out,
-                                const er_solve_opts &opt, er_batch_stats *stats, cudaStream_t us, int dev,
-                                std::chrono::steady_clock::time_point t0) {
-    std::vector<int> order((size_t)n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return grids[a]->d.n > grids[b]->d.n; });
-    int64_t nmax = 0;
-    for (int c = 0; c < n; ++c) nmax = std::max<int64_t>(nmax, grids[c]->d.n);
-    cudaEvent_t ev_in;
-    ER_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
-    ER_CUDA(cudaEventRecord(ev_in, us));  // the workers start after the caller's prior work
-
-    std::atomic<int> next{0};
-    std::atomic<bool> stop{false};
-    std::mutex mu;
-    er_status first = ER_OK;  // first hard error (mu)
-    std::string first_msg;
-    bool any_unconverged = false;
-    int32_t iters = 0, reps = 0, conv = 0, launches = 0, captures = 0;
-    int64_t nodes = 0;
-    double mx = 0.0;
-    auto record_error = [&](er_status e, const char *what) {
-        std::lock_guard<std::mutex> g(mu);
-        if (first == ER_OK) {
-            first = e;
-            first_msg = std::string(what) + ": " + er_last_error();
-        }
-        stop = true;
-    };
-    auto worker = [&]() {
-        if (cudaSetDevice(dev) != cudaSuccess) return record_error(ER_ERR_CUDA, "cudaSetDevice");
-        cudaStream_t st = nullptr;
-        void *Y = nullptr, *Z = nullptr;
-        const size_t bytes = (size_t)nmax * (size_t)k * sizeof(float);
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaStreamWaitEvent(st, ev_in, 0) != cudaSuccess ||
-            cudaMalloc(&Y, bytes) != cudaSuccess || cudaMalloc(&Z, bytes) != cudaSuccess) {
-            record_error(ER_ERR_OOM, "batch worker setup");
-        } else {
-            for (int q = next.fetch_add(1); q < n && !stop; q = next.fetch_add(1)) {
-                const int c = order[(size_t)q];
-                er_solve_stats ss{};
-                er_status e = sketch(grids[c], k, seed + (uint64_t)c, ER_FP32_REFINE, Y, st);
-                if (e != ER_OK) {
-                    record_error(e, "er_sketch");
-                    break;
-                }
-                e = solve(grids[c], Y, Z, k, ER_FP32_REFINE, &opt, &ss, st);
-                const bool unconv = e == ER_ERR_NOT_CONVERGED;
-                if (e != ER_OK && !unconv) {
-                    record_error(e, "er_solve");
-                    break;
-                }
-                e = reff_map(grids[c], Z, k, ER_FP32_REFINE, R_out[c], st);
-                if (e == ER_OK && cudaStreamSynchronize(st) != cudaSuccess) e = fail(ER_ERR_CUDA, "cudaStreamSynchronize");
-                if (e != ER_OK) {
-                    record_error(e, "er_reff_map");
-                    break;
-                }
-                std::lock_guard<std::mutex> g(mu);
-                any_unconverged |= unconv;
-                iters = std::max(iters, ss.iterations);
-                reps = std::max(reps, ss.sweeps);
-                conv += ss.converged_cols == k;
-                nodes += grids[c]->d.n - grids[c]->d.n_floating;
-                mx = std::max(mx, ss.max_rel_residual);
-                for (int i = 0; i < ER_N_PASS; ++i) launches += ss.launches[i];
-                launches += 2;  // sketch and map
-            }
-        }
-        if (st) cudaStreamSynchronize(st);
-        if (Y) cudaFree(Y);
-        if (Z) cudaFree(Z);
-        if (st) cudaStreamDestroy(st);
-    };
-    const int nw = std::min<int>(kMgWorkers, n);
-    std::vector<std::thread> pool;
-    pool.reserve((size_t)nw);
-    try {
-        for (int i = 0; i < nw; ++i) pool.emplace_back(worker);
-    } catch (const std::exception &) {  // no thread could be started: the started ones finish
-        if (pool.empty()) {
-            for (auto &t : pool) t.join();
-            cudaEventDestroy(ev_in);
-            return fail(ER_ERR_OOM, "could not start a host worker thread");
-        }
-    }
-    for (auto &t : pool) t.join();
-    cudaEventDestroy(ev_in);
-    if (first != ER_OK) return fail(first, first_msg);
-    if (stats) {
-        stats->n_grids = n;
-        stats->iterations = iters;
-        stats->replacements = reps;
-        stats->converged = conv;
-        stats->nodes = nodes;
-        stats->max_rel_residual = mx;
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        stats->launches = launches;
-        stats->graph_captures = captures;
-    }
-    if (any_unconverged) return fail(ER_ERR_NOT_CONVERGED, "maxit reached with networks still above tol");
-    return ER_OK;
-}
 
 static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, er_precision prec,
                              const int32_t *tile_rows, double *const *R_out, const er_solve_opts *o,
@@ -173,7 +58,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
             if (grids[d] == grids[c]) return fail(ER_ERR_INVALID_ARG, "a grid appears twice (precond 1 solves networks concurrently)");
     }
     ER_CUDA(cudaSetDevice(dev));
-    if (opt.precond == 1) return batch_solve_mg(grids, n, k, seed, R_out, opt, stats, us, dev, t0);
+    if (opt.precond == 1) return mg_batch_graph(grids, n, k, seed, tile_rows, R_out, opt, stats, us, t0);
     cudaStream_t s = nullptr;
     ER_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct StreamGuard {

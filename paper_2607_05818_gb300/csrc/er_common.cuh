@@ -316,6 +316,19 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
 
 // er_fp32.cu: the FP32 form's passes (all asynchronous on w.s)
 er_status fp32_prepare(const GridDev &g, Workspace &w, const void *Yt, void *Z);
+// er_sketch / er_reff_map on a stream (er_grid.cu)
+er_status sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt, cudaStream_t s);
+er_status reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R, cudaStream_t s);
+// er_solve with the grid's lock already held (er_pcg.cu)
+er_status solve_locked(er_grid *g, const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts *opts,
+                       er_solve_stats *stats, cudaStream_t us);
+// the grid's cached solve workspace for (k, precision, tiling), allocated on first use
+er_status get_workspace(GridDev *g, int k, er_precision prec, int rows, int order, Workspace **out);
+// the multigrid batching form: every network's sketch, multigrid solve and map in one CUDA
+// graph, each network's iteration loop a device-side conditional (er_mg.cu)
+er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, const int32_t *tile_rows,
+                         double *const *R_out, const er_solve_opts &opt, er_batch_stats *stats, cudaStream_t us,
+                         std::chrono::steady_clock::time_point t0);
 void fp32_init(const GridDev &g, Workspace &w, const void *Yt, void *Z, double tol, Prof *pf);
 int fp32_iterate(const GridDev &g, Workspace &w, void *Z, double tol, int cur, Prof *pf);
 void fp32_accum(const GridDev &g, Workspace &w, void *Z, Prof *pf);

@@ -81,12 +81,13 @@ __device__ inline void sketch_term(double (&acc)[4], uint64_t key, int64_t e, in
 // Y^T[i][j] = sum over edges e at node i of sigma_e(i) sqrt(w_e) Q[j][e]; one thread per
 // (node, 4 columns).  Edges are visited in canonical-id order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sketch(SketchView g, int k, uint64_t key, double rk, T *Yt) {
+__global__ void __launch_bounds__(256) k_sketch(SketchView g, int k, int j_off, uint64_t key, double rk, T *Yt) {
     const int64_t nq = k / 4;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.n * nq) return;
     const int64_t i = tid / nq;
-    const int j0 = (int)(tid - i * nq) * 4;
+    const int jl = (int)(tid - i * nq) * 4;  // stored column; the sketch row hashed is j_off + jl
+    const int j0 = j_off + jl;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (!g.floating[i]) {
         const int x = (int)(i % g.W);
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) k_sketch(SketchView g, int k, uint64_t ke
         for (int e = g.pad_ptr[i]; e < g.pad_ptr[i + 1]; ++e)
             sketch_term(acc, key, g.pad_eid[e], j0, sqrt(g.pad_g[e]) * rk);
     }
-    T *out = Yt + i * k + j0;
+    T *out = Yt + i * k + jl;
     if constexpr (sizeof(T) == 8) {
         reinterpret_cast<double2 *>(out)[0] = make_double2(acc[0], acc[1]);
         reinterpret_cast<double2 *>(out)[1] = make_double2(acc[2], acc[3]);
@@ -162,12 +163,13 @@ struct SketchAcc32 {
     }
 };
 
-__global__ void __launch_bounds__(256) k_sketch32(SketchView g, int k, uint64_t key, float2 rk, float *Yt) {
+__global__ void __launch_bounds__(256) k_sketch32(SketchView g, int k, int j_off, uint64_t key, float2 rk, float *Yt) {
     const int64_t nq = k / 4;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.n * nq) return;
     const int64_t i = tid / nq;
-    const int j0 = (int)(tid - i * nq) * 4;
+    const int jl = (int)(tid - i * nq) * 4;  // stored column; the sketch row hashed is j_off + jl
+    const int j0 = j_off + jl;
     SketchAcc32 acc;
     if (!g.floating[i]) {
         const int x = (int)(i % g.W);
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(256) k_sketch32(SketchView g, int k, uint64_t 
             acc.term(key, g.tsv_eid[e], j0, g.sq_tsv[e], rk, g.tsv_sgn[e] <= 0);
         for (int e = g.pad_ptr[i]; e < g.pad_ptr[i + 1]; ++e) acc.term(key, g.pad_eid[e], j0, g.sq_pad[e], rk, false);
     }
-    reinterpret_cast<float4 *>(Yt + i * k + j0)[0] =
+    reinterpret_cast<float4 *>(Yt + i * k + jl)[0] =
         make_float4(__fadd_rn(acc.S[0], acc.C[0]), __fadd_rn(acc.S[1], acc.C[1]), __fadd_rn(acc.S[2], acc.C[2]),
                     __fadd_rn(acc.S[3], acc.C[3]));
 }
@@ -442,6 +444,12 @@ er_status grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv, 
     int device = (opt && opt->device >= 0) ? opt->device : -1;
     if (device >= 0) ER_CUDA(cudaSetDevice(device));
     ER_CUDA(cudaGetDevice(&device));
+    // the no-allocation solve's static workspace on this device: resolved (its module loaded,
+    // its memory committed) here, at set-up, so that no er_solve_noalloc call does it
+    {
+        const er_status ps = noalloc_prepare(device);
+        if (ps != ER_OK) return ps;
+    }
     er_grid *g = new er_grid();
     GridDev &d = g->d;
     d.T = T; d.W = W; d.H = H; d.n = n;
@@ -507,25 +515,34 @@ er_status check_nk(const er_grid *g, int32_t k, const void *p, const char *name)
     return ER_OK;
 }
 
-er_status sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt, cudaStream_t s) {
-    er_status st = check_nk(g, k, Yt, "Yt");
+// columns j0 .. j0 + k_local - 1 of the k_total-column sketch (scale 1/sqrt(k_total)), stored
+// as a [n][k_local] array
+er_status sketch_cols(er_grid *g, int32_t k_total, int32_t j0, int32_t k_local, uint64_t seed, er_precision prec,
+                      void *Yt, cudaStream_t s) {
+    er_status st = check_nk(g, k_local, Yt, "Yt");
     if (st != ER_OK) return st;
     if (prec != ER_FP64 && prec != ER_FP32_REFINE) return fail(ER_ERR_INVALID_ARG, "bad precision");
+    if (j0 < 0 || k_total < 1 || (int64_t)j0 + k_local > (int64_t)k_total)
+        return fail(ER_ERR_INVALID_ARG, "need 0 <= j0 and j0 + k_local <= k_total");
     const GridDev &d = g->d;
     ER_CUDA(cudaSetDevice(d.device));
-    const int64_t threads = d.n * (k / 4);
+    const int64_t threads = d.n * (k_local / 4);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     const uint64_t key = splitmix64(seed);
-    const double rk = 1.0 / std::sqrt((double)k);
+    const double rk = 1.0 / std::sqrt((double)k_total);
     if (prec == ER_FP64)
-        k_sketch<double><<<blocks, 256, 0, s>>>(sketch_view(d), k, key, rk, (double *)Yt);
+        k_sketch<double><<<blocks, 256, 0, s>>>(sketch_view(d), k_local, j0, key, rk, (double *)Yt);
     else {
         const float rk_hi = (float)rk;
         const float2 rk2 = make_float2(rk_hi, (float)(rk - (double)rk_hi));
-        k_sketch32<<<blocks, 256, 0, s>>>(sketch_view(d), k, key, rk2, (float *)Yt);
+        k_sketch32<<<blocks, 256, 0, s>>>(sketch_view(d), k_local, j0, key, rk2, (float *)Yt);
     }
     ER_CUDA(cudaGetLastError());
     return ER_OK;
+}
+
+er_status sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt, cudaStream_t s) {
+    return sketch_cols(g, k, 0, k, seed, prec, Yt, s);
 }
 
 er_status reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R, cudaStream_t s) {
@@ -605,6 +622,11 @@ er_status er_grid_info(const er_grid *g, int64_t *n_nodes, int64_t *n_floating, 
 
 er_status er_sketch(er_grid *g, int32_t k, uint64_t seed, er_precision prec, void *Yt, void *stream) {
     return er::sketch(g, k, seed, prec, Yt, (cudaStream_t)stream);
+}
+
+er_status er_sketch_cols(er_grid *g, int32_t k_total, int32_t j0, int32_t k_local, uint64_t seed, er_precision prec,
+                         void *Yt, void *stream) {
+    return er::sketch_cols(g, k_total, j0, k_local, seed, prec, Yt, (cudaStream_t)stream);
 }
 
 er_status er_reff_map(er_grid *g, const void *Z, int32_t k, er_precision prec, double *R, void *stream) {

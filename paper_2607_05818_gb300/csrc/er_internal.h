@@ -91,6 +91,10 @@ void free_workspace(GridDev *g);
 // er_mg.cu
 void free_mg(GridDev *g);
 
+// er_noalloc.cu: look up the device address of the no-allocation solve's static workspace on
+// `device` (the current device) once; later calls return at once
+er_status noalloc_prepare(int device);
+
 // er_grid.cu: grid assembly behind er_grid_create
 er_status grid_create(const er_tier *tiers, int32_t n_tiers, const er_tsv *tsv, int64_t n_tsv,
                       const er_pad *pads, int64_t n_pads, const er_options *opt, cudaStream_t stream,

@@ -3,11 +3,13 @@
 //
 // The workspace (residual, two search directions, the stencil product, per-tile partial
 // dot products, per-column scalars, flags and tickets) is carved out of one file-scope
-// __device__ array of fixed size.  Every process that loads the library holds this array
-// on every GPU it touches until the process exits.  All calls share it, so the counters
-// and flags it carries are cleared at the start of each call; the call is blocking and
-// serialised by a process-wide lock, and a call must not overlap on the GPU with another
-// use of the array.
+// __device__ array of fixed size.  The CUDA runtime loads the module that holds it lazily,
+// on the first lookup of its address; er_grid_create does that lookup for its device
+// (noalloc_prepare), so the array is committed when the first grid on a device is created
+// and held until the process exits, and no er_solve_noalloc call loads a module or commits
+// memory.  All calls share the array, so the counters and flags it carries are cleared at
+// the start of each call; the call is blocking and serialised by a process-wide lock, and a
+// call must not overlap on the GPU with another use of the array.
 #include <chrono>
 #include <mutex>
 
@@ -30,22 +32,26 @@ constexpr size_t kNaBytes = 4 * kNaVec + kNaPart + kNaScal + kNaInts + kNaCnt;  
 
 static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
-static std::mutex g_na_mu;
-static void *g_na_ptr[64];  // device address of g_na_scratch, per device ordinal
+static std::mutex g_na_mu;      // serialises the solves that use the array
+static std::mutex g_na_setup_mu;
+static void *g_na_ptr[64];      // device address of g_na_scratch, per device ordinal
 
 // Once per device, with that device current: the host-side name of the array is not a
 // device address, so ask the runtime for it.
 static er_status na_setup(int dev, unsigned char **out) {
     if (dev < 0 || dev >= 64) return fail(ER_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_na_setup_mu);
     if (!g_na_ptr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
         g_na_ptr[dev] = p;
     }
-    *out = static_cast<unsigned char *>(g_na_ptr[dev]);
+    if (out) *out = static_cast<unsigned char *>(g_na_ptr[dev]);
     return ER_OK;
 }
+
+er_status noalloc_prepare(int device) { return na_setup(device, nullptr); }
 
 static er_status solve_noalloc(er_grid *gg, const void *Yt, void *Z, int32_t k, const er_solve_opts *o,
                                er_solve_stats *stats, cudaStream_t s) {
@@ -91,6 +97,9 @@ static er_status solve_noalloc(er_grid *gg, const void *Yt, void *Z, int32_t k, 
     ER_CUDA(cudaMemsetAsync(w.ints, 0, kNaInts, s));
     ER_CUDA(cudaMemsetAsync(w.counter, 0, kNaCnt, s));
     st = solve_core(g, w, Yt, Z, ER_FP64, opt, stats, t0);
+    // an error can return before the stream drains: the next call's clearing of the array
+    // must not overlap kernels of this one still in flight, so wait while the lock is held
+    if (st != ER_OK) cudaStreamSynchronize(s);
     w.r[0] = w.p[0] = w.p[1] = w.q = nullptr;  // nothing here belongs to the workspace cache
     w.part = w.scal = nullptr;
     w.ints = nullptr;

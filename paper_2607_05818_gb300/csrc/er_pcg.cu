@@ -290,7 +290,7 @@ void free_workspace(GridDev *g) {
     g->ws = nullptr;
 }
 
-static er_status get_workspace(GridDev *g, int k, er_precision prec, int rows, int order, Workspace **out) {
+er_status get_workspace(GridDev *g, int k, er_precision prec, int rows, int order, Workspace **out) {
     const int es = prec == ER_FP64 ? 8 : 4;
     const Tiling want = make_tiling(*g, k, es, rows, order);
     if (g->ws && g->ws->k == k && g->ws->prec == prec && g->ws->til.rows == want.rows &&
@@ -436,16 +436,27 @@ er_status check_solve_args(const void *Yt, void *Z, int32_t k, er_precision prec
 
 er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts *o,
                 er_solve_stats *stats, cudaStream_t us) {
+    if (!gg) return fail(ER_ERR_INVALID_ARG, "grid is NULL");
+    std::lock_guard<std::mutex> lock(gg->mu);
+    return solve_locked(gg, Yt, Z, k, prec, o, stats, us);
+}
+
+// er_solve with the grid's lock already held by the caller
+er_status solve_locked(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision prec, const er_solve_opts *o,
+                       er_solve_stats *stats, cudaStream_t us) {
     auto t0 = std::chrono::steady_clock::now();
     if (!gg) return fail(ER_ERR_INVALID_ARG, "grid is NULL");
     er_solve_opts opt = o ? *o : er_default_solve_opts(prec);
     er_status st = check_solve_args(Yt, Z, k, prec, opt);
     if (st != ER_OK) return st;
-    std::lock_guard<std::mutex> lock(gg->mu);
     GridDev &g = gg->d;
     ER_CUDA(cudaSetDevice(g.device));
+    // a grid of at most 512 nodes is the multigrid's coarsest level itself, and 1 x 1 tiers do
+    // not coarsen: both use Jacobi
+    const bool mg = opt.precond == 1 && g.n > 512 && std::max(g.W, g.H) > 1;
     Workspace *wp = nullptr;
-    st = get_workspace(&g, k, prec, opt.tile_rows, opt.block_order, &wp);
+    // multigrid: tile_rows sets the finest level's V-cycle rows, not the accurate residual's tiling
+    st = get_workspace(&g, k, prec, mg ? 0 : opt.tile_rows, opt.block_order, &wp);
     if (st != ER_OK) {
         free_workspace(&g);
         return st;
@@ -459,9 +470,6 @@ er_status solve(er_grid *gg, const void *Yt, void *Z, int32_t k, er_precision pr
     ER_CUDA(cudaStreamWaitEvent(w.s, w.ev, 0));
     std::vector<double> resid((size_t)k);
     w.h_resid = resid.data();
-    // a grid of at most 512 nodes is the multigrid's coarsest level itself, and 1 x 1 tiers do
-    // not coarsen: both use Jacobi
-    const bool mg = opt.precond == 1 && g.n > 512 && std::max(g.W, g.H) > 1;
     st = mg ? mg_solve_core(g, w, Yt, Z, opt, stats, t0) : solve_core(g, w, Yt, Z, prec, opt, stats, t0);
     w.h_resid = nullptr;
     return st;

@@ -65,6 +65,7 @@ struct er_surrogate {
     float *out = nullptr, *dout = nullptr;
     double *loss = nullptr;
     int step = 0;
+    int tile_n = 0;                      // requested N-tile width of the convolutions (0: automatic)
     std::vector<void *> owned;           // activation buffers
 };
 
@@ -153,9 +154,14 @@ static er_status ensure_batch(er_surrogate *s, int B) {
     return ER_OK;
 }
 
+// the N-tile width requested by the surrogate whose pass runs on this thread (forward and
+// backward set it from er_surrogate::tile_n)
+static thread_local int g_tile_n = 0;
+
 static UConv fwd_conv(const Conv &c, const __nv_bfloat16 *x1, int c1, int x1_half, const __nv_bfloat16 *x2, int c2,
                       int B, int h, int w, __nv_bfloat16 *y) {
     UConv u;
+    u.tile_n = g_tile_n;
     u.x1 = x1; u.c1 = c1; u.x1_half = x1_half; u.x2 = x2; u.c2 = c2;
     u.w = c.wb; u.bias = c.b; u.nb = B; u.h = h; u.w_ = w; u.cout = c.cout; u.relu = 1; u.y = y;
     return u;
@@ -163,6 +169,7 @@ static UConv fwd_conv(const Conv &c, const __nv_bfloat16 *x1, int c1, int x1_hal
 
 static er_status forward(er_surrogate *s, const __nv_bfloat16 *maps, int B, cudaStream_t st) {
     const int L = s->L;
+    g_tile_n = s->tile_n;
     for (int l = 0; l < L; ++l) {
         const int h = s->ea[l].h, w = s->ea[l].w, c = s->ea[l].c;
         const __nv_bfloat16 *in = l == 0 ? maps : s->pool[l - 1].a;
@@ -190,6 +197,7 @@ static er_status forward(er_surrogate *s, const __nv_bfloat16 *maps, int B, cuda
 static UConv dgrad_conv(const Conv &c, const __nv_bfloat16 *dy, int B, int h, int w, __nv_bfloat16 *g1,
                         const __nv_bfloat16 *m1, int c1, int m1_half, __nv_bfloat16 *g2, const __nv_bfloat16 *m2) {
     UConv u;
+    u.tile_n = g_tile_n;
     u.x1 = dy; u.c1 = c.cout; u.w = c.wt; u.nb = B; u.h = h; u.w_ = w; u.cout = c.cin;
     u.g1 = g1; u.m1 = m1; u.c1o = c1; u.m1_half = m1_half; u.g2 = g2; u.m2 = m2;
     return u;
@@ -204,6 +212,7 @@ static UConv wgrad_in(const __nv_bfloat16 *x1, int c1, int x1_half, const __nv_b
 
 static er_status backward(er_surrogate *s, const __nv_bfloat16 *maps, int B, cudaStream_t st) {
     const int L = s->L, H = s->shape.H, W = s->shape.W;
+    g_tile_n = s->tile_n;
     const int64_t M0 = (int64_t)B * H * W;
     // zero the weight gradients
     for (auto *v : {&s->enc, &s->dec})
@@ -482,6 +491,115 @@ er_status er_surrogate_train_step(er_surrogate *s, const void *maps, const float
     ER_CUDA(er::unet_adam(s->hb, s->hmb, s->hvb, s->hgb, s->shape.out_ch, lr, b1, b2, eps, step, nullptr, nullptr, 1, 1, cs));
     ER_CUDA(cudaStreamSynchronize(cs));
     return ER_OK;
+}
+
+er_status er_surrogate_set_tile_n(er_surrogate *s, int32_t tile_n) {
+    if (!s) return er::fail(ER_ERR_INVALID_ARG, "surrogate is NULL");
+    if (tile_n != 0 && tile_n != 32 && tile_n != 64 && tile_n != 96 && tile_n != 128 && tile_n != 192 && tile_n != 256)
+        return er::fail(ER_ERR_INVALID_ARG, "tile_n must be 0, 32, 64, 96, 128, 192 or 256");
+    s->tile_n = tile_n;
+    return ER_OK;
+}
+
+er_status er_conv_launch_counts(int64_t *counts, int32_t n, int32_t reset) {
+    if (n < 0 || (n > 0 && !counts)) return er::fail(ER_ERR_INVALID_ARG, "counts is NULL");
+    er::unet_conv_counts(counts, n, reset);
+    return ER_OK;
+}
+
+}  // extern "C"
+
+// ---- single convolution layers ----------------------------------------------------------
+
+namespace er {
+
+static er_status conv_layer_args(const void *a, const void *b, const void *out, int B, int H, int W, int cin,
+                                 int cout, int tile_n) {
+    if (!a || !b || !out) return fail(ER_ERR_INVALID_ARG, "input, weight/gradient and output pointers are required");
+    if ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)out)) & 15u)
+        return fail(ER_ERR_INVALID_ARG, "device arrays must be 16-byte aligned");
+    if (B < 1 || H < 1 || W < 1 || cin < 32 || cin % 32 || cout < 32 || cout % 32)
+        return fail(ER_ERR_INVALID_ARG, "need B, H, W >= 1 and cin, cout positive multiples of 32");
+    if ((int64_t)B * H * W > (int64_t)1 << 31) return fail(ER_ERR_INVALID_ARG, "B*H*W must be below 2^31");
+    if (tile_n != 0 && tile_n != 32 && tile_n != 64 && tile_n != 96 && tile_n != 128 && tile_n != 192 && tile_n != 256)
+        return fail(ER_ERR_INVALID_ARG, "tile_n must be 0, 32, 64, 96, 128, 192 or 256");
+    return ER_OK;
+}
+
+// BF16 copies of FP32 weights [cout][3][3][cin]: as stored, and flipped and transposed for the
+// data gradient; freed in stream order by the caller through conv_weights_free
+static er_status conv_weights(const float *w, int cout, int cin, cudaStream_t s, __nv_bfloat16 **wb,
+                              __nv_bfloat16 **wt) {
+    const int64_t n = (int64_t)cout * 9 * cin;
+    *wb = *wt = nullptr;
+    ER_CUDA(cudaMallocAsync((void **)wb, (size_t)n * 2, s));
+    ER_CUDA(cudaMallocAsync((void **)wt, (size_t)n * 2, s));
+    ER_CUDA(unet_to_bf16(w, *wb, *wt, n, cout, cin, s));
+    return ER_OK;
+}
+
+static er_status layer_done(cudaStream_t s, __nv_bfloat16 *wb, __nv_bfloat16 *wt, cudaError_t launch) {
+    if (wb) cudaFreeAsync(wb, s);
+    if (wt) cudaFreeAsync(wt, s);
+    if (launch != cudaSuccess) return cuda_fail(launch, "convolution launch");
+    return check_kernels(s);
+}
+
+}  // namespace er
+
+extern "C" {
+
+er_status er_conv3x3_forward(const void *x, const float *w, const float *bias, int32_t B, int32_t H, int32_t W,
+                             int32_t cin, int32_t cout, int32_t relu, int32_t tile_n, void *y, er_conv_info *info,
+                             void *stream) {
+    using namespace er;
+    er_status st = conv_layer_args(x, w, y, B, H, W, cin, cout, tile_n);
+    if (st != ER_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    __nv_bfloat16 *wb = nullptr, *wt = nullptr;
+    st = conv_weights(w, cout, cin, cs, &wb, &wt);
+    if (st != ER_OK) return layer_done(cs, wb, wt, cudaSuccess), st;
+    UConvInfo ui;
+    UConv u;
+    u.x1 = (const __nv_bfloat16 *)x; u.c1 = cin; u.w = wb; u.bias = bias; u.nb = B; u.h = H; u.w_ = W;
+    u.cout = cout; u.relu = relu != 0; u.y = (__nv_bfloat16 *)y; u.tile_n = tile_n; u.info = &ui;
+    const cudaError_t e = unet_conv3x3(u, cs);
+    st = layer_done(cs, wb, wt, e);
+    if (st == ER_OK && info) *info = er_conv_info{ui.kernel, ui.bn, ui.bk, 0};
+    return st;
+}
+
+er_status er_conv3x3_dgrad(const void *dy, const float *w, const void *x, int32_t B, int32_t H, int32_t W,
+                           int32_t cin, int32_t cout, int32_t tile_n, void *dx, er_conv_info *info, void *stream) {
+    using namespace er;
+    er_status st = conv_layer_args(dy, w, dx, B, H, W, cin, cout, tile_n);
+    if (st != ER_OK) return st;
+    if (!x || ((uintptr_t)x & 15u)) return fail(ER_ERR_INVALID_ARG, "x (the forward input) must be a 16-byte aligned device array");
+    cudaStream_t cs = (cudaStream_t)stream;
+    __nv_bfloat16 *wb = nullptr, *wt = nullptr;
+    st = conv_weights(w, cout, cin, cs, &wb, &wt);
+    if (st != ER_OK) return layer_done(cs, wb, wt, cudaSuccess), st;
+    UConvInfo ui;
+    UConv u;
+    u.x1 = (const __nv_bfloat16 *)dy; u.c1 = cout; u.w = wt; u.nb = B; u.h = H; u.w_ = W; u.cout = cin;
+    u.g1 = (__nv_bfloat16 *)dx; u.m1 = (const __nv_bfloat16 *)x; u.c1o = cin; u.tile_n = tile_n; u.info = &ui;
+    const cudaError_t e = unet_conv3x3(u, cs);
+    st = layer_done(cs, wb, wt, e);
+    if (st == ER_OK && info) *info = er_conv_info{ui.kernel, ui.bn, ui.bk, 0};
+    return st;
+}
+
+er_status er_conv3x3_wgrad(const void *x, const void *dy, int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
+                           float *dw, void *stream) {
+    using namespace er;
+    er_status st = conv_layer_args(x, dy, dw, B, H, W, cin, cout, 0);
+    if (st != ER_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    ER_CUDA(cudaMemsetAsync(dw, 0, (size_t)cout * 9 * cin * sizeof(float), cs));
+    UConv u;
+    u.x1 = (const __nv_bfloat16 *)x; u.c1 = cin; u.nb = B; u.h = H; u.w_ = W; u.cout = cout;
+    const cudaError_t e = unet_wgrad3x3(u, (const __nv_bfloat16 *)dy, dw, cs);
+    return layer_done(cs, nullptr, nullptr, e);
 }
 
 }  // extern "C"

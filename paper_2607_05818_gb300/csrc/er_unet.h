@@ -9,6 +9,12 @@
 
 namespace er {
 
+// What a convolution launch ran: kernel 1 = persistent TMA kernel, 2 = cp.async-staged
+// kernel; bn = output channels per tile (N of the MMA); bk = input channels per K step.
+struct UConvInfo {
+    int kernel = 0, bn = 0, bk = 0;
+};
+
 // One 3x3 convolution launch (forward, or dgrad when y is null; see er_unet_kernels.cu).
 struct UConv {
     const __nv_bfloat16 *x1 = nullptr, *x2 = nullptr;
@@ -20,6 +26,8 @@ struct UConv {
     __nv_bfloat16 *g1 = nullptr, *g2 = nullptr;
     const __nv_bfloat16 *m1 = nullptr, *m2 = nullptr;
     int c1o = 0, m1_half = 0;
+    int tile_n = 0;             // requested output channels per tile (0: automatic)
+    UConvInfo *info = nullptr;  // filled with what ran (nullable)
 };
 
 // 3x3 convolution (forward, or dgrad when y is null) on tcgen05 with the accumulator in
@@ -34,6 +42,10 @@ cudaError_t unet_upsample2x(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, in
 cudaError_t unet_conv3x3_mma(const UConv &c, cudaStream_t s);
 // copy the kernels' error word (non-zero: a bounded wait expired) to *host, clear it, sync
 cudaError_t unet_take_error(int *host, cudaStream_t s);
+// launches of the convolution kernels since the last reset: [0..5] persistent TMA kernel with
+// 32-channel K steps and N tiles of 32, 64, 96, 128, 192, 256; [6..11] the same with 64-channel
+// K steps; [12] cp.async-staged kernel; [13] weight gradient
+void unet_conv_counts(int64_t *out, int n, int reset);
 cudaError_t unet_wgrad3x3(const UConv &c, const __nv_bfloat16 *dy, float *dw, cudaStream_t s);
 cudaError_t unet_maxpool(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s);
 cudaError_t unet_maxpool_bwd(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int nb, int h, int w,

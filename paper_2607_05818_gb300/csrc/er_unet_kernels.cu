@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "er_internal.h"
@@ -1078,6 +1079,22 @@ static int tc_tile_n(int64_t mtiles, int cout) {
     return pick;
 }
 
+// a requested N-tile width is honoured when it is one the kernels support and divides cout
+static bool tile_n_ok(int bn, int cout) {
+    return (bn == 32 || bn == 64 || bn == 96 || bn == 128 || bn == 192 || bn == 256) && bn <= cout && cout % bn == 0;
+}
+
+static std::atomic<long long> g_conv_counts[16];
+
+static int width_slot(int bn) { return bn == 32 ? 0 : bn == 64 ? 1 : bn == 96 ? 2 : bn == 128 ? 3 : bn == 192 ? 4 : 5; }
+
+void unet_conv_counts(int64_t *out, int n, int reset) {
+    for (int i = 0; i < 16; ++i) {
+        const long long v = reset ? g_conv_counts[i].exchange(0) : g_conv_counts[i].load();
+        if (out && i < n) out[i] = (int64_t)v;
+    }
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -1145,6 +1162,7 @@ static cudaError_t launch_conv_tc(const UConv &c, int bx, int by, int bimg, cuda
         bn = cand;
         if (tiles_m * (c.cout / cand) >= nsm) break;
     }
+    if (c.tile_n && tile_n_ok(c.tile_n, c.cout)) bn = c.tile_n;
     if (bn == 0) return cudaErrorInvalidValue;
     const int bnp = bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
     const int stg = TBM * BK * 2 + bn * BK * 2;
@@ -1197,7 +1215,12 @@ static cudaError_t launch_conv_tc(const UConv &c, int bx, int by, int bimg, cuda
     if (!a.err) return cudaErrorInvalidSymbol;
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
     k_conv_tc<BK><<<grid, 192, smem, s>>>(mx1, mx2, mw, a);
-    return cudaGetLastError();
+    const cudaError_t le = cudaGetLastError();
+    if (le == cudaSuccess) {
+        g_conv_counts[(BK == 64 ? 6 : 0) + width_slot(bn)].fetch_add(1);
+        if (c.info) *c.info = UConvInfo{1, bn, BK};
+    }
+    return le;
 }
 
 cudaError_t unet_upsample2x(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s) {
@@ -1225,7 +1248,7 @@ cudaError_t unet_conv3x3_stage(const UConv &c, cudaStream_t s) {
     const int cin = c.c1 + c.c2;
     const int64_t M = (int64_t)c.nb * c.h * c.w_;
     const int64_t mtiles = (M + TBM - 1) / TBM;
-    const int bn = tc_tile_n(mtiles, c.cout);
+    const int bn = c.tile_n && tile_n_ok(c.tile_n, c.cout) ? c.tile_n : tc_tile_n(mtiles, c.cout);
     if (cin % TBK || c.c1 % TBK || bn == 0) return cudaErrorInvalidValue;
     int *err = err_word();
     if (!err) return cudaErrorInvalidSymbol;
@@ -1243,7 +1266,12 @@ cudaError_t unet_conv3x3_stage(const UConv &c, cudaStream_t s) {
     const int tcols = bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256;
     const int smem = TSTAGES * (TBM * TBK * 2 + bn * TBK * 2) + 1024;
     k_conv3x3_tc<<<dim3((unsigned)mtiles, (unsigned)(c.cout / bn)), 128, smem, s>>>(a, bn, tcols, err);
-    return cudaGetLastError();
+    const cudaError_t le = cudaGetLastError();
+    if (le == cudaSuccess) {
+        g_conv_counts[12].fetch_add(1);
+        if (c.info) *c.info = UConvInfo{2, bn, TBK};
+    }
+    return le;
 }
 
 cudaError_t unet_conv3x3_mma(const UConv &c, cudaStream_t s) {
@@ -1286,7 +1314,9 @@ cudaError_t unet_wgrad3x3(const UConv &c, const __nv_bfloat16 *dy, float *dw, cu
     a.pix_per_split = ((M + splits - 1) / splits + WBK - 1) / WBK * WBK;
     splits = (M + a.pix_per_split - 1) / a.pix_per_split;
     k_wgrad3x3<<<dim3(gx, gy, (unsigned)splits), 128, smem, s>>>(a);
-    return cudaGetLastError();
+    const cudaError_t le = cudaGetLastError();
+    if (le == cudaSuccess) g_conv_counts[13].fetch_add(1);
+    return le;
 }
 
 cudaError_t unet_maxpool(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s) {

@@ -92,6 +92,14 @@ class er_unet_shape(ctypes.Structure):
                 ("W", c_int32)]
 
 
+class er_conv_info(ctypes.Structure):
+    _fields_ = [("kernel", c_int32), ("tile_n", c_int32), ("k_step", c_int32), ("reserved", c_int32)]
+
+    def as_dict(self):
+        return {"kernel": {1: "tma", 2: "staged"}.get(self.kernel, self.kernel), "tile_n": self.tile_n,
+                "k_step": self.k_step}
+
+
 _S = c_int32  # er_status
 _sig = {
     "er_default_solve_opts": (er_solve_opts, [c_int32]),
@@ -100,6 +108,7 @@ _sig = {
     "er_grid_destroy": (_S, [c_void_p]),
     "er_grid_info": (_S, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "er_sketch": (_S, [c_void_p, c_int32, c_uint64, c_int32, c_void_p, c_void_p]),
+    "er_sketch_cols": (_S, [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_int32, c_void_p, c_void_p]),
     "er_solve": (_S, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(er_solve_opts),
                       POINTER(er_solve_stats), c_void_p]),
     "er_solve_noalloc": (_S, [c_void_p, c_void_p, c_void_p, c_int32, POINTER(er_solve_opts),
@@ -125,6 +134,13 @@ _sig = {
                                c_void_p]),
     "er_surrogate_train_step": (_S, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
                                      POINTER(c_double), c_void_p]),
+    "er_surrogate_set_tile_n": (_S, [c_void_p, c_int32]),
+    "er_conv3x3_forward": (_S, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                c_int32, c_void_p, POINTER(er_conv_info), c_void_p]),
+    "er_conv3x3_dgrad": (_S, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                              c_void_p, POINTER(er_conv_info), c_void_p]),
+    "er_conv3x3_wgrad": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "er_conv_launch_counts": (_S, [POINTER(c_int64), c_int32, c_int32]),
     "er_pad_currents": (_S, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "er_stack_pairs": (_S, [POINTER(er_stack), c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                             POINTER(er_stack_stats), c_void_p]),
@@ -252,6 +268,23 @@ def grid_create(inst, device: int = -1, stream=None) -> Grid:
 def sketch(grid: Grid, k: int, seed: int, prec, Yt, stream=None):
     return _check(_lib.er_sketch(grid.handle, k, c_uint64(seed), PRECISIONS[prec], _ptr(Yt), _stream(stream)),
                   "er_sketch")
+
+
+def sketch_cols(grid: Grid, k_total: int, j0: int, k_local: int, seed: int, prec, Yt, stream=None):
+    """Columns j0 .. j0 + k_local - 1 of the k_total-column sketch into Yt [n][k_local]."""
+    return _check(_lib.er_sketch_cols(grid.handle, k_total, j0, k_local, c_uint64(seed), PRECISIONS[prec], _ptr(Yt),
+                                      _stream(stream)), "er_sketch_cols")
+
+
+def column_shard(k: int, world: int, rank: int) -> tuple[int, int]:
+    """(j0, k_local) of rank's share of k sketch columns over `world` ranks: contiguous, disjoint,
+    covering 0 .. k-1, each a multiple of 4 columns (the last ranks may get 4 fewer)."""
+    if k % 4 or k < 4 * world:
+        raise ValueError("k must be a multiple of 4 with at least 4 columns per rank")
+    q = k // 4
+    base, extra = divmod(q, world)
+    j0 = 4 * (rank * base + min(rank, extra))
+    return j0, 4 * (base + (1 if rank < extra else 0))
 
 
 def solve(grid: Grid, Yt, Z, k: int, prec, opts: er_solve_opts | None = None, stream=None, allow_unconverged=False):
@@ -400,6 +433,9 @@ class Surrogate:
         self._steps += 1
         return loss.value
 
+    def set_tile_n(self, tile_n: int) -> None:
+        _check(_lib.er_surrogate_set_tile_n(self.handle, int(tile_n)), "er_surrogate_set_tile_n")
+
     def destroy(self):
         if getattr(self, "handle", None):
             _lib.er_surrogate_destroy(self.handle)
@@ -410,6 +446,39 @@ class Surrogate:
             self.destroy()
         except Exception:
             pass
+
+
+def conv3x3_forward(x, w, bias, B, H, W, cin, cout, y, relu=True, tile_n=0, stream=None) -> dict:
+    """One surrogate convolution layer: x, y BF16 [B][H][W][c] device tensors, w FP32
+    [cout][3][3][cin], bias FP32 [cout] or None.  Returns what ran."""
+    info = er_conv_info()
+    _check(_lib.er_conv3x3_forward(_ptr(x), _ptr(w), _ptr(bias), B, H, W, cin, cout, int(bool(relu)), tile_n, _ptr(y),
+                                   ctypes.byref(info), _stream(stream)), "er_conv3x3_forward")
+    return info.as_dict()
+
+
+def conv3x3_dgrad(dy, w, x, B, H, W, cin, cout, dx, tile_n=0, stream=None) -> dict:
+    """Data gradient of that layer through the ReLU of its input x."""
+    info = er_conv_info()
+    _check(_lib.er_conv3x3_dgrad(_ptr(dy), _ptr(w), _ptr(x), B, H, W, cin, cout, tile_n, _ptr(dx),
+                                 ctypes.byref(info), _stream(stream)), "er_conv3x3_dgrad")
+    return info.as_dict()
+
+
+def conv3x3_wgrad(x, dy, B, H, W, cin, cout, dw, stream=None) -> None:
+    """Weight gradient of that layer into dw (FP32 [cout][3][3][cin], overwritten)."""
+    _check(_lib.er_conv3x3_wgrad(_ptr(x), _ptr(dy), B, H, W, cin, cout, _ptr(dw), _stream(stream)), "er_conv3x3_wgrad")
+
+
+CONV_COUNT_SLOTS = ([f"tma_k32_n{n}" for n in (32, 64, 96, 128, 192, 256)]
+                    + [f"tma_k64_n{n}" for n in (32, 64, 96, 128, 192, 256)] + ["staged", "wgrad", "-", "-"])
+
+
+def conv_launch_counts(reset=False) -> dict:
+    """Launches of the convolution kernels since the last reset, by kernel, K step and N tile."""
+    a = (c_int64 * 16)()
+    _check(_lib.er_conv_launch_counts(a, 16, int(bool(reset))), "er_conv_launch_counts")
+    return {name: int(v) for name, v in zip(CONV_COUNT_SLOTS, a) if name != "-"}
 
 
 def release_pool():

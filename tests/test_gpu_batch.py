@@ -79,9 +79,11 @@ def test_batch_rejects_fp64_and_bad_args(er):
 
 
 def test_multigrid_batch_equals_single_solves(er):
-    """precond = 1: every network is solved by er_solve's multigrid form (several at a time on
-    worker streams), so each map is bitwise the map of sketch + solve + map on that network
-    alone, and within the FP32 form's bound of the oracle."""
+    """precond = 1: every network's sketch + multigrid solve + map is one branch of a single
+    CUDA graph, its iteration loop a device-side conditional node, with exactly er_solve's
+    kernels and decisions; so each map is bitwise the map of sketch + solve + map on that
+    network alone, and within the FP32 form's bound of the oracle.  Networks too small for a
+    hierarchy (the 5 x 3 and 20 x 19 ones) take er_solve's Jacobi path, as alone."""
     nets = make_batch()
     k, seed = 32, 515
     grids = [er.grid_create(n) for n in nets]
@@ -106,5 +108,43 @@ def test_multigrid_batch_equals_single_solves(er):
         assert np.array_equal(np.isfinite(got), fin)
         if fin.any():
             assert np.max(np.abs(got[fin] / ref[fin] - 1)) <= 1e-3, c
+    for g in grids:
+        g.destroy()
+
+
+def test_multigrid_autotuned_rows_are_valid_and_change_only_speed(er, tmp_path, monkeypatch):
+    """The autotuner's choice of the finest prolongation's rows per CTA, per size class, is one
+    of its candidates, and the maps it gives are bitwise those of the library's default, both
+    for er_solve and for the batching form (the dot partials are kept per 8-row group)."""
+    monkeypatch.setenv("ER_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_2607_05818_gb300 import autotune
+    rng = np.random.default_rng(2025)
+    nets = [I.batch_candidate(rng, 0, T=2, W=64, n_tsv=60), I.batch_candidate(rng, 1, T=3, W=128, n_tsv=200),
+            I.batch_candidate(rng, 2, T=4, W=64, n_tsv=100, clustered=True)]
+    k, seed = 32, 99
+    rows = [autotune.best_mg_rows(n, k) for n in nets]
+    print(f"tuned rows {rows}; timings {autotune._load()}")
+    assert all(r in autotune.CANDIDATE_MG_ROWS for r in rows)
+    grids = [er.grid_create(n) for n in nets]
+    opts = er.default_solve_opts("fp32", precond=1, check_every=2)
+    R0 = [torch.empty(n.n, dtype=torch.float64, device="cuda") for n in nets]
+    R1 = [torch.empty(n.n, dtype=torch.float64, device="cuda") for n in nets]
+    er.batch_solve(grids, k, seed, R0, opts=opts)
+    er.batch_solve(grids, k, seed, R1, opts=opts, tile_rows=rows)
+    torch.cuda.synchronize()
+    for a, b in zip(R0, R1):
+        assert torch.equal(a, b)
+    # er_solve with every candidate row count: the same map
+    net, g = nets[1], grids[1]
+    Y = torch.empty((net.n, k), dtype=torch.float32, device="cuda")
+    er.sketch(g, k, seed, "fp32", Y)
+    outs = []
+    for r in autotune.CANDIDATE_MG_ROWS:
+        Z = torch.empty_like(Y)
+        er.solve(g, Y, Z, k, "fp32", er.default_solve_opts("fp32", precond=1, check_every=2, tile_rows=r))
+        outs.append(Z)
+    torch.cuda.synchronize()
+    for Z in outs[1:]:
+        assert torch.equal(Z, outs[0])
     for g in grids:
         g.destroy()

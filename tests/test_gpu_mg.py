@@ -87,22 +87,6 @@ def test_mg_cuts_iterations_and_is_deterministic(er):
     assert rel_err(Rm, Rj) <= 5e-4
 
 
-def test_mg_full_size_sampled(er):
-    """4x512x512, k = 256 as the bench runs it: R at sampled nodes against exact sparse
-    solves of the oracle (same seed)."""
-    inst = I.precision_4x512()
-    k, seed = 256, inst.meta["seed"]
-    R, st = run(er, inst, k, seed, 1, profile=1)
-    rng = np.random.default_rng(0)
-    nodes = np.unique(np.concatenate([rng.integers(0, inst.n, 10), [0, inst.n - 1, 3 * 262144 + 300]]))
-    f = exact.SparseFactor(inst)
-    R_ref, _ = osk.reff_jl_sampled(f, osk.sketch(inst, k, seed), nodes)
-    err = np.abs(R[nodes] / R_ref - 1)
-    print(f"multigrid full size: iterations {st['iterations']} sweeps {st['sweeps']} max err {err.max():.2e}")
-    assert err.max() <= 1e-3
-    assert st["launches"][er.PASS_MG] > 0
-
-
 def test_mg_option_rules(er):
     inst = I.tiny_plain()
     g = er.grid_create(inst)

@@ -3,8 +3,8 @@
 Sketch: element by element against the oracle's FP64 sketch.  Solve + map: the FP64
 path against the oracle's same-seed JL estimate (dense Cholesky solves) within 1e-9
 relative, the FP32+refinement path within 1e-3 relative; ragged sizes, ragged RHS
-blocks, floating nodes, a single node and the host-buffer entry point; at the full
-4x512x512 size, sampled rows against exact sparse solves of the oracle.
+blocks, floating nodes, a single node and the host-buffer entry point.  The full-size
+workloads are in test_gpu_fullsize.py.
 """
 import numpy as np
 import pytest
@@ -163,74 +163,28 @@ def test_invalid_device_arguments(er):
     g.destroy()
 
 
-def test_full_size_precision_workload_sampled(er):
-    """4x512x512, k=256, FP32+refinement as the bench runs it: sketch rows and R at sampled
-    nodes against the oracle (exact sparse solves, same seed)."""
-    inst = I.precision_4x512()
-    k, seed = 256, inst.meta["seed"]
-    Yt_ref = osk.sketch(inst, k, seed)
-    Yt, Z, R, st = gpu_map(er, inst, k, seed, "fp32")
-    rng = np.random.default_rng(0)
-    nodes = np.unique(np.concatenate([rng.integers(0, inst.n, 12), [0, inst.n - 1, 511, 3 * 262144 + 300]]))
-    np.testing.assert_allclose(Yt[nodes], Yt_ref[nodes].astype(np.float32).astype(np.float64), rtol=1.2e-7)
-    del Yt, Z
-    f = exact.SparseFactor(inst)
-    R_ref, Z_ref = osk.reff_jl_sampled(f, Yt_ref, nodes)
-    err = np.abs(R[nodes] / R_ref - 1)
-    print(f"full-size FP32+refine: iterations {st['iterations']} sweeps {st['sweeps']} "
-          f"max rel residual {st['max_rel_residual']:.2e}; sampled R max rel err {err.max():.2e}")
-    assert err.max() <= 1e-3
-
-
-def test_full_size_large_workload_properties(er):
-    """8x1024x1024 (8,388,608 nodes, 10% of segments open, 20,000 TSV columns), k=256, the
-    FP32 form.  The oracle cannot factor this network, so it checks what holds at any size:
-    sketch rows at sampled nodes (oracle gather over incident edges); the FP64 residual
-    y_j - G z_j of sampled columns with the oracle's G, within the stopping tolerance plus
-    the FP32 rounding of the conductances and of Z; R against the row norms of Z; and the
-    floating nodes, exactly."""
-    import scipy.sparse as sp
-
-    inst = I.large_8x1024()
-    k, seed = 256, inst.meta["seed"]
-    opts = er.default_solve_opts("fp32")
-    g = er.grid_create(inst)
-    Yt = torch.empty((inst.n, k), dtype=F32, device=DEV)
-    Z = torch.empty_like(Yt)
-    R = torch.empty(inst.n, dtype=F64, device=DEV)
-    er.sketch(g, k, seed, "fp32", Yt)
-    _, st = er.solve(g, Yt, Z, k, "fp32", opts)
-    er.reff_map(g, Z, k, "fp32", R)
-    torch.cuda.synchronize()
-    g.destroy()
-    floating = network.floating_mask(inst)
-    Rh = R.cpu().numpy()
-    assert np.array_equal(~np.isfinite(Rh), floating)
-    rng = np.random.default_rng(8)
-    T, W, H = inst.T, inst.W, inst.H
-    special = [0, inst.n - 1, W - 1, (T - 1) * W * H + (H - 1) * W,
-               int(network.node_id(T, W, H, inst.tsv_tier[0], inst.tsv_y[0], inst.tsv_x[0])),
-               int(network.node_id(T, W, H, inst.pad_tier[3], inst.pad_y[3], inst.pad_x[3])),
-               int(np.flatnonzero(floating)[0])]
-    nodes = np.unique(np.concatenate([rng.integers(0, inst.n, 24), special]))
-    idx = torch.as_tensor(nodes, device=DEV)
-    Ys, Zs = Yt[idx].double().cpu().numpy(), Z[idx].double().cpu().numpy()
-    np.testing.assert_allclose(Ys, osk.sketch_rows(inst, nodes, k, seed).astype(np.float32).astype(np.float64),
-                               rtol=1.2e-7, atol=0)
-    fin = np.isfinite(Rh[nodes])
-    np.testing.assert_allclose(Rh[nodes][fin], np.sum(Zs[fin] ** 2, axis=1), rtol=1e-12)
-    G = network.conductance_matrix(inst)
-    Gabs = abs(G)
-    dinv = 1.0 / np.maximum(G.diagonal(), 1e-300)
-    u = 2.0 ** -24
-    for j in (0, 101, 255):
-        y = Yt[:, j].double().cpu().numpy()
-        z = Z[:, j].double().cpu().numpy()
-        r = y - G @ z
-        nrm = lambda v: float(np.sqrt(np.sum(v * v * dinv)))
-        bound = 1.05 * opts.tol * nrm(y) + 2.2 * u * nrm(Gabs @ np.abs(z))
-        print(f"column {j}: |r|/|y| = {nrm(r) / nrm(y):.2e}, bound {bound / nrm(y):.2e}")
-        assert nrm(r) <= bound
-    print(f"large 8x1024x1024: iterations {st['iterations']}, replacements {st['sweeps']}, "
-          f"max rel residual {st['max_rel_residual']:.2e}, {floating.sum()} floating nodes")
-    assert st["max_rel_residual"] <= opts.tol
+def test_column_shards_sum_to_the_map(er):
+    """Column sharding of one network (the multi-GPU partition): each shard's sketch columns are
+    bitwise the same columns of the whole sketch, and the shards' partial maps add up to the
+    whole map.  The shards run one after another on one GPU; across GPUs the sum is one
+    all-reduce of the n-vector."""
+    inst = I.random_small(np.random.default_rng(31), T=3, W=37, H=23, n_tsv=40, n_pads=3, open_frac=0.1)
+    k, seed, world = 48, 123, 3
+    for prec, dt in (("fp64", F64), ("fp32", F32)):
+        Y_full, _, R_full, _ = gpu_map(er, inst, k, seed, prec)
+        g = er.grid_create(inst)
+        R_sum = np.zeros(inst.n)
+        for rank in range(world):
+            j0, kl = er.column_shard(k, world, rank)
+            Yt = torch.empty((inst.n, kl), dtype=dt, device=DEV)
+            Z = torch.empty_like(Yt)
+            R = torch.empty(inst.n, dtype=F64, device=DEV)
+            er.sketch_cols(g, k, j0, kl, seed, prec, Yt)
+            er.solve(g, Yt, Z, kl, prec)
+            er.reff_map(g, Z, kl, prec, R)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(Yt.cpu().numpy().astype(np.float64), Y_full[:, j0:j0 + kl])
+            R_sum += R.cpu().numpy()
+        g.destroy()
+        tol = 1e-12 if prec == "fp64" else 1e-3
+        assert rel_err(R_sum, R_full) <= tol, (prec, rel_err(R_sum, R_full))

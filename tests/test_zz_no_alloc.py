@@ -1,6 +1,7 @@
 """er_solve_noalloc through the C ABI: the FP64 solve whose workspace is a fixed static
 device array, for callers that cannot allocate device memory at solve time.  Two calls
-in a row must match er_solve (same kernels and tiling, so the same iterates), and an
+in a row must match er_solve (same kernels and tiling, so the same iterates), neither may
+change the device's free memory (the array is committed when the grid is created), and an
 oversized request must be rejected.  Collected last on purpose."""
 import ctypes
 
@@ -35,13 +36,19 @@ def test_noalloc_solve_matches_er_solve_twice(er):
     ref = Z_ref.cpu().numpy()
     scale = np.maximum(np.abs(ref).max(axis=0), 1e-300)
     stream = torch.cuda.current_stream().cuda_stream
+    Zs = [torch.full_like(Yt, float("nan")) for _ in range(2)]   # outputs allocated up front
+    torch.cuda.synchronize()
     for call in range(2):
-        Z = torch.full_like(Yt, float("nan"))
+        Z = Zs[call]
         stats = er.er_solve_stats()
+        free_before = torch.cuda.mem_get_info()[0]
         status = er._lib.er_solve_noalloc(g.handle, Yt.data_ptr(), Z.data_ptr(), k, None, ctypes.byref(stats),
                                           stream)
         assert status == er.ER_OK, (call, er.status_str(status), er._lib.er_last_error())
         torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+        # no device allocation: any cudaMalloc moves the free figure by at least a 2 MiB page
+        assert free_before - free_after < (1 << 20), (call, free_before, free_after)
         got = Z.cpu().numpy()
         assert np.max(np.abs(got - ref) / scale) <= 1e-9, call
         assert stats.iterations == st_ref["iterations"] and stats.converged_cols == k
