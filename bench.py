@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--sur-screen", type=int, default=4096, help="surrogate workload: screened candidates")
     p.add_argument("--sur-k", type=int, default=64, help="surrogate workload: JL columns of labels and verification")
     p.add_argument("--sur-epochs", type=int, default=12)
+    p.add_argument("--sur-recall", type=int, default=512, help="surrogate workload: candidates solved exactly "
+                                                                "to measure the screen's recall (untimed)")
     p.add_argument("--workers", type=int, default=8, help="spawned processes encoding candidate maps")
     return p.parse_args()
 
@@ -260,9 +262,15 @@ def gpu_index(local_rank):
 
 
 def kernel_source_hash():
+    """Hash of the solver kernels' device code: the multigrid kernels (er_mg.cu up to its host
+    section), the FP32 and FP64 passes and their shared device helpers.  A change there makes
+    the committed DRAM counters stale."""
     h = hashlib.sha256()
-    for f in ("er_pcg.cu", "er_fp32.cu", "er_mg.cu", "er_common.cuh", "er_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2607_05818_gb300", "csrc", f), "rb").read())
+    for f in ("er_pcg.cu", "er_fp32.cu", "er_mg.cu", "er_common.cuh"):
+        text = open(os.path.join(ROOT, "paper_2607_05818_gb300", "csrc", f), "rb").read()
+        if f == "er_mg.cu":
+            text = text.split(b"// ---- tensor maps of the tiled kernels")[0]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
@@ -309,7 +317,7 @@ def run_batch(args, rank, world, local_rank):
     if not args.no_autotune:  # per size class (tiers, W, H), measured once, outside the timed region
         from paper_2607_05818_gb300 import autotune
         tt = time.perf_counter()
-        rows = [autotune.best_mg_rows(c, k) if use_mg else autotune.best_rows(c, k) for c in cands]
+        rows = [autotune.best_mg_order(c, k) if use_mg else autotune.best_rows(c, k) for c in cands]
         t_tune = time.perf_counter() - tt
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -334,7 +342,7 @@ def run_batch(args, rank, world, local_rank):
     value = n_job * args.steps / s_max
     # the other mode of er_batch_solve, one call (outside the timed region)
     o0 = time.perf_counter()
-    st_other = er.batch_solve(grids, k, 1, R, opts=opts_other, tile_rows=rows)[1]
+    st_other = er.batch_solve(grids, k, 1, R, opts=opts_other)[1]  # library default launch shape
     torch.cuda.synchronize()
     other_s = time.perf_counter() - o0
     # sequential: each candidate's sketch + solve + map on its own (second call, warm workspace),
@@ -373,8 +381,9 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": f"batch_candidates_{len(cands)}", "k": k, "candidates": len(cands),
                    "nodes": n_ok, "iterations": last["iterations"], "converged": last["converged"],
                    "graph_captures": last["graph_captures"],
-                   "tile_rows": (f"autotuned per size class ({len(set(rows))} distinct choices, "
-                                 f"{t_tune:.1f} s to tune, untimed)" if rows else "library default"),
+                   "launch_shape": (f"autotuned per size class ({'launch order' if use_mg else 'tile rows'}: "
+                                    f"{sorted(set(rows))}, {t_tune:.1f} s to tune, untimed)" if rows
+                                    else "library default"),
                    "max_rel_residual": last["max_rel_residual"],
                    "mode": "multigrid: one CUDA graph, each network's loop a device-side conditional node"
                    if use_mg else "Jacobi: shared launches over a (network, tile) work list"},
@@ -497,6 +506,32 @@ def run_surrogate(args, rank, world, local_rank):
     pn = pred.index_select(0, torch.as_tensor(flagged, device=dev)).cpu().numpy()
     errs = [S.rel_errors(pn[j], Rv[j], insts[j]) for j in range(len(flagged))]
     allerr = np.concatenate(errs)
+    # screening recall on a bounded sample (untimed): the first n_rec candidates solved exactly,
+    # ranked by the same statistic as the screen (largest log R); how many of the truly worst
+    # 5% the surrogate's worst 5% (and 10%) contain
+    n_rec = min(args.sur_recall, args.sur_screen)
+    t_rec = time.perf_counter()
+    true_score = []
+    for lo in range(0, n_rec, 64):
+        part = [S.candidate_at(seed_sc, i, T, W) for i in range(lo, min(lo + 64, n_rec))]
+        grids = [er.grid_create(n) for n in part]
+        Rr = [torch.empty(n.n, dtype=torch.float64, device=dev) for n in part]
+        er.batch_solve(grids, k, 1 + lo, Rr)
+        for r_ in Rr:
+            r_ = r_.cpu().numpy()
+            true_score.append(float(np.log(r_[np.isfinite(r_)].max())))
+        for g_ in grids:
+            g_.destroy()
+    true_score = np.array(true_score)
+    pred_score = pred[:n_rec].amax(dim=(1, 2, 3)).cpu().numpy()
+    q = max(1, int(round(0.05 * n_rec)))
+    worst = set(np.argsort(-true_score)[:q].tolist())
+    order = np.argsort(-pred_score)
+    recall = {"sample": f"the first {n_rec} screened candidates, solved exactly (k={k}), {time.perf_counter() - t_rec:.1f} s",
+              "worst_5pct": q, "in_surrogate_worst_5pct": len(worst & set(order[:q].tolist())) / q,
+              "in_surrogate_worst_10pct": len(worst & set(order[:2 * q].tolist())) / q,
+              "rank_correlation": float(np.corrcoef(np.argsort(np.argsort(true_score)),
+                                                    np.argsort(np.argsort(pred_score)))[0, 1])}
     flops = unet_conv_flops(L, C, in_ch, W, W) * args.sur_screen
     ach = flops / (fwd_ms / 1e3) / 1e12
     pk = load_peaks()
@@ -520,6 +555,7 @@ def run_surrogate(args, rank, world, local_rank):
         "gain_over_exact": value / exact,
         "surrogate_only": {"value": args.sur_screen * n_nodes / fwd_s, "unit": UNIT,
                            "forward_ms_per_candidate": fwd_ms / args.sur_screen},
+        "screening_recall": recall,
         "surrogate_error_vs_solver": {
             "max_rel_err": float(allerr.max()), "mean_rel_err": float(allerr.mean()),
             "flagged_mean_rel_err": float(np.concatenate(errs[:nv]).mean()),
@@ -990,7 +1026,7 @@ def run_ours(args, rank, world, local_rank):
         kinds = [(1, "k_mg_upd_tile<true>", 6 * nk * es + coef),    # p', r, x, p'_prev in; r, x out
                  (4, "k_mg_upd_tile<false>", 3 * nk * es + coef),   # p', r in; r out
                  (0, "k_mg_dir_tile", 3 * nk * es + coef),          # z, p in; p' out
-                 (7, "k_mg_sweep<true> (finest level)", int(2.25 * nk * es) + coef),
+                 (7, "k_mg_tile<true, true> (finest level)", int(2.25 * nk * es) + coef),
                  (6, "k_mg_tile<false, false> (finest level)", int(1.25 * nk * es) + coef),
                  (5, "V-cycle on the coarse levels", int(3.5 * nk * es / 3)),
                  (2, "k_tma<MODE_R> (double-float residual)", 4 * nk * es + coef)]  # x {hi, lo}, b in; r out

@@ -107,12 +107,10 @@ typedef struct {
     int32_t profile;       /* 1: time every pass with CUDA events on the solver's stream
                               (disables graphs); fills er_solve_stats.kernel_ms */
     int32_t tile_rows;     /* Jacobi: y rows swept by one CTA of the stencil passes (0 = default
-                              64; clipped to H).  Multigrid: rows per CTA of the finest level's
-                              prolongation (rounded down to a multiple of 8; 0 = automatic); its
-                              dot partials are kept per 8-row group, so this changes the speed,
-                              not the result */
-    int32_t block_order;   /* 0 default, 1 RHS column blocks of a tile adjacent in launch
-                              order, 2 column blocks outermost */
+                              64; clipped to H); ignored by the multigrid form */
+    int32_t block_order;   /* launch order of the tiled kernels: 0 default, 1 RHS column blocks
+                              of a tile adjacent, 2 column blocks outermost.  The multigrid
+                              kernels give bitwise the same result in either order */
     int32_t precond;       /* 0 Jacobi (D^-1); 1 aggregation multigrid: one V-cycle per
                               iteration (ER_FP32_REFINE only; see er_solve) */
 } er_solve_opts;
@@ -260,13 +258,13 @@ typedef struct {
  *     ends it when the network's columns meet tol (the accurate residual replacement runs under
  *     a nested IF node exactly when er_solve's host loop would run it), so converged networks
  *     leave the GPU while the others continue.  Each map equals the single-network map
- *     bitwise.  Every network needs more than 512 nodes and a tier wider than one node; a
- *     grid may appear only once (ER_ERR_INVALID_ARG otherwise).  tile_rows[c] (nullable; 0 =
- *     automatic) sets the rows per CTA of network c's finest-level prolongation (the
- *     autotuner's choice; rounded down to a multiple of 8; it changes the speed, not the
- *     result).  Each grid keeps its solve workspace and hierarchy cached (as after er_solve);
- *     the sketch and Z arrays of all networks are allocated for the call and freed before it
- *     returns. */
+ *     bitwise.  Networks of at most 512 nodes (their own coarsest level) are solved first
+ *     with er_solve's Jacobi path, as alone.  A grid may appear only once
+ *     (ER_ERR_INVALID_ARG otherwise).  tile_rows[c] (nullable) is network c's launch order
+ *     as er_solve_opts.block_order (the autotuner's choice per size class; 0 = opts'); it
+ *     changes the speed, not the result.  Each grid keeps its solve workspace and hierarchy
+ *     cached (as after er_solve); the sketch and Z arrays of all networks are allocated for
+ *     the call and freed before it returns. */
 er_status er_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, er_precision prec,
                          const int32_t *tile_rows, double *const *R_out, const er_solve_opts *opts,
                          er_batch_stats *stats, void *stream);
@@ -350,13 +348,16 @@ er_status er_conv3x3_dgrad(const void *dy, const float *w, const void *x, int32_
                            int32_t cin, int32_t cout, int32_t tile_n, void *dx, er_conv_info *info, void *stream);
 /* Weight gradient of that layer: dw[o][ky][kx][c] = sum_{b,h,w} dy[b][h][w][o]
  * x[b][h+ky-1][w+kx-1][c] (zero padding), FP32 [cout][3][3][cin] device array, overwritten.
- * x and dy are BF16 device arrays as above; products accumulate in FP32.  Synchronises. */
+ * x and dy are BF16 device arrays as above; products accumulate in FP32 (on the tcgen05
+ * tensor cores when cout is a multiple of 128, cin of 64 and B*H*W tiles into 64-pixel
+ * boxes, else on warp-level MMA), split over pixel ranges whose sums are added atomically.
+ * Synchronises. */
 er_status er_conv3x3_wgrad(const void *x, const void *dy, int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,
                            float *dw, void *stream);
 /* Launches of the convolution kernels in this process since the last reset (host counters):
  * [0..5] persistent TMA kernel with 32-channel K steps and N tiles of 32, 64, 96, 128, 192,
  * 256; [6..11] the same with 64-channel K steps; [12] cp.async-staged kernel; [13] weight
- * gradient; [14..15] zero.  The first min(n, 16) are written to counts; reset != 0 zeroes them. */
+ * gradient on warp-level mma.sync; [14] weight gradient on tcgen05; [15] zero.  The first min(n, 16) are written to counts; reset != 0 zeroes them. */
 er_status er_conv_launch_counts(int64_t *counts, int32_t n, int32_t reset);
 
 /* R_i = sum_j Z_ij^2 into device array R [n] (FP64); +inf for floating nodes.

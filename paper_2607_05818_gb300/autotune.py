@@ -1,11 +1,12 @@
-"""Autotuner for the tile shapes of the solve's stencil kernels (y rows swept per CTA).
+"""Autotuner for the launch shape of the solve's stencil kernels, per network size class.
 
-For a network size class (tiers, width, height, k, precision, preconditioner) it times a
-few PCG iterations through the C ABI for each candidate row count, with the library's own
-per-pass CUDA-event timing (er_solve_opts.profile), and keeps the fastest:
-  - Jacobi: the rows of the stencil passes A and B (best_rows);
-  - multigrid: the rows of the finest level's prolongation (best_mg_rows), whose partial
-    dot products are kept per 8-row group, so the choice changes the speed and not the map.
+For a size class (tiers, width, height, k, precision, preconditioner) it times a few PCG
+iterations through the C ABI for each candidate, with the library's own per-pass CUDA-event
+timing (er_solve_opts.profile), and keeps the fastest:
+  - Jacobi: the y rows swept by one CTA of the stencil passes (best_rows);
+  - multigrid: the launch order of the tiled V-cycle and CG kernels, the RHS column blocks of
+    a tile adjacent or outermost (best_mg_order).  The order decides which CTAs share L2 lines,
+    not the arithmetic, so the tuned solve gives bitwise the map of the untuned one.
 Results are cached in a JSON file (ER_AUTOTUNE_CACHE, default ~/.cache/er3d_autotune.json),
 keyed by the size class, so each class is measured once per machine.
 """
@@ -16,7 +17,7 @@ import os
 import threading
 
 CANDIDATE_ROWS = (16, 32, 64, 128)
-CANDIDATE_MG_ROWS = (8, 16, 32, 64)
+CANDIDATE_MG_ORDERS = (1, 2)  # er_solve_opts.block_order: column blocks adjacent, outermost
 _lock = threading.Lock()
 
 
@@ -85,8 +86,8 @@ def best_rows(inst, k: int, prec: str = "fp32") -> int:
         return int(rows)
 
 
-def measure_mg(inst, k: int, iters: int = 6, rows_list=CANDIDATE_MG_ROWS) -> dict:
-    """Per-launch time (ms) of the finest-level prolongation for each candidate row count."""
+def measure_mg(inst, k: int, iters: int = 6, orders=CANDIDATE_MG_ORDERS) -> dict:
+    """Per-iteration kernel time (ms) of the multigrid solve for each candidate launch order."""
     import torch
 
     from . import er
@@ -95,30 +96,29 @@ def measure_mg(inst, k: int, iters: int = 6, rows_list=CANDIDATE_MG_ROWS) -> dic
     Z = torch.empty_like(Y)
     er.sketch(g, k, 1, "fp32", Y)
     out = {}
-    for rows in rows_list:
-        if rows > max(8, inst.H) and rows != rows_list[0]:
-            continue
+    for order in orders:
         best = None
         for _ in range(2):
-            o = er.default_solve_opts("fp32", precond=1, maxit=iters, profile=1, tile_rows=rows,
+            o = er.default_solve_opts("fp32", precond=1, maxit=iters, profile=1, block_order=order,
                                       replace_every=10 ** 6)
             _, st = er.solve(g, Y, Z, k, "fp32", o, allow_unconverged=True)
-            t = st["kernel_ms"][er.PASS_MG_UP] / max(st["launches"][er.PASS_MG_UP], 1)
+            t = sum(st["kernel_ms"]) / max(st["iterations"], 1)
             best = t if best is None else min(best, t)
-        out[rows] = best
+        out[order] = best
     g.destroy()
     return out
 
 
-def best_mg_rows(inst, k: int) -> int:
-    """The cached best multigrid prolongation row count for this size class."""
+def best_mg_order(inst, k: int) -> int:
+    """The cached best launch order (er_solve_opts.block_order) of the multigrid kernels for
+    this size class."""
     kk = key(inst, k, "fp32") + "_mg"
     with _lock:
         d = _load()
         if kk in d:
-            return int(d[kk]["rows"])
+            return int(d[kk]["order"])
         times = measure_mg(inst, k)
-        rows = min(times, key=times.get)
-        d[kk] = {"rows": int(rows), "ms_per_launch": {str(r): t for r, t in times.items()}}
+        order = min(times, key=times.get)
+        d[kk] = {"order": int(order), "ms_per_iteration": {str(r): t for r, t in times.items()}}
         _store(d)
-        return int(rows)
+        return int(order)

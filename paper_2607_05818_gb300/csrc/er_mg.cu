@@ -56,6 +56,8 @@ constexpr int kMinCtas = 1216;       // small levels: fewer steps, so at least 8
 
 struct Lvl {  // one level's device arrays (kernel argument)
     int T, W, H;
+    int cb_outer;        // launch order of the tiled kernels: 0 column blocks of a tile adjacent,
+                         // 1 column blocks outermost (the same arithmetic either way)
     int64_t n;
     const float4 *coef;  // {+-1/d, gE, gS, pad}; sign < 0: the node has TSV segments
     const int32_t *tsv_ptr, *tsv_nbr;
@@ -186,9 +188,10 @@ __device__ __forceinline__ TileGeo tile_geo(const Lvl &C, int k, int &tile) {
     const int ncb = (k + TCB - 1) / TCB;
     const int tx = (C.W + TAX - 1) / TAX, ty = (C.H + TAY - 1) / TAY;
     TileGeo g;
-    int b = blockIdx.x / ncb;
+    const int ntile = tx * ty * C.T;
+    int b = C.cb_outer ? (int)(blockIdx.x % ntile) : (int)(blockIdx.x / ncb);
     tile = b;
-    g.c0 = (blockIdx.x % ncb) * TCB;
+    g.c0 = (C.cb_outer ? (int)(blockIdx.x / ntile) : (int)(blockIdx.x % ncb)) * TCB;
     g.X0 = (b % tx) * TAX;
     b /= tx;
     g.Y0 = (b % ty) * TAY;
@@ -351,245 +354,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUte
     }
 }
 
-// ---- row-streamed prolongation on the finest level ------------------------------------------
-//
-// The prolongation and post-sweep of k_mg_tile, with the rows streamed instead of whole tiles,
-// for the finest level (the largest kernel of the V-cycle).  A CTA owns 30 nodes along x of one
-// tier (slots 1..30 of 32; slots 0 and 31 are the halo) and a run of `rows` y rows (a multiple
-// of 8), for 32 RHS columns.  One thread issues cp.async.bulk.tensor copies of whole rows into
-// a ring of SW_NS shared-memory stages, each completed through an mbarrier: r and the
-// coefficients over the 32 slots and the coarse correction row under them (17 aggregates).
-// Thread (slot, column group) forms the smoothed value v = w D^-1 r + s P z_c of its node in
-// the current row once, keeps the rows above in registers and publishes v in a two-row shared
-// ring for its x-neighbours, so every v is evaluated exactly once; G v of the row above is
-// finished from registers (north, centre, south) and the ring (west, east), and
-// z = v + w D^-1 (r - G v) is written.  The partials of r.z are kept per (30-node strip,
-// 8-row group, tier), so the rows per CTA do not change the reduction order.  Every wait is
-// bounded; on expiry the CTA raises the error word, stops issuing copies, drains its own
-// copies and returns.
-
-constexpr int SW_NX = 32, SW_NXI = 30;  // node slots per CTA along x; owned slots
-constexpr int SW_NS = 5;                // stages in flight
-constexpr int SW_ZX = 17;               // coarse aggregates under the 32 slots
-constexpr int SW_OFF_R = 0, SW_OFF_C = SW_NX * TCB * 4, SW_OFF_Z = SW_OFF_C + SW_NX * 16;
-constexpr int SW_STAGE = ((SW_OFF_Z + SW_ZX * TCB * 4 + 127) / 128) * 128;  // 6,912 bytes
-constexpr int SW_RING = 2 * SW_NX * TCB * 4;                                // v of two rows
-constexpr int SW_PAIR = SW_NX * TCB * 4;                                    // r.z runs of an 8-row group
-constexpr int SW_SMEM = SW_NS * SW_STAGE + SW_RING + SW_PAIR + 128;
-
-struct SwGeo {
-    int tile, tiles_x, tiles_y, tx, t, c0, xb, y0, y1;
-};
-
-int sw_tiles_x(const Lvl &F) { return (F.W + SW_NXI - 1) / SW_NXI; }
-// the prolongation's dot partials: one per (30-node column strip, 8-row group, tier), whatever the
-// rows per CTA (a multiple of 8), so the reduction order does not depend on the launch shape
-int64_t sw_groups(const Lvl &F) { return (int64_t)sw_tiles_x(F) * ((F.H + 7) / 8) * F.T; }
-int64_t sw_tiles(const Lvl &F, int rows) { return (int64_t)sw_tiles_x(F) * ((F.H + rows - 1) / rows) * F.T; }
-dim3 sw_grid(const Lvl &F, int k, int rows) { return dim3((unsigned)(sw_tiles(F, rows) * ((k + TCB - 1) / TCB))); }
-
-// rows per CTA on level F: the largest even count up to 64 that still gives every SM about
-// eight CTAs (small levels), at least 2
-int sw_rows(const Lvl &F, int k) {
-    const int64_t want = 8 * 152;
-    int rows = 64;
-    while (rows > 2 && sw_tiles(F, rows) * ((k + TCB - 1) / TCB) < want) rows >>= 1;
-    return rows;
-}
-
-__device__ __forceinline__ SwGeo sw_geo(const Lvl &F, int k, int rows) {
-    const int ncb = (k + TCB - 1) / TCB;
-    SwGeo g;
-    g.tiles_x = (F.W + SW_NXI - 1) / SW_NXI;
-    g.tiles_y = (F.H + rows - 1) / rows;
-    int b = blockIdx.x / ncb;
-    g.tile = b;
-    g.c0 = (blockIdx.x % ncb) * TCB;
-    const int tx = b % g.tiles_x;
-    g.tx = tx;
-    b /= g.tiles_x;
-    const int ty = b % g.tiles_y;
-    g.t = b / g.tiles_y;
-    g.xb = SW_NXI * tx - 1;
-    g.y0 = ty * rows;
-    g.y1 = min(g.y0 + rows, F.H);
-    return g;
-}
-
-// mbarrier helpers of the sweep: plain arrive (one per warp) and a bounded wait that also gives
-// up as soon as another thread of the CTA has raised the abort flag
-__device__ __forceinline__ void sw_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mg_saddr(b)) : "memory");
-}
-__device__ __forceinline__ bool sw_wait(uint64_t *b, uint32_t parity, int *s_abort, int *err) {
-    for (uint32_t spins = 0; !mg_try_wait(b, parity);) {
-        if (*reinterpret_cast<volatile int *>(s_abort)) return false;
-        if (++spins > kTileSpin) {
-            *reinterpret_cast<volatile int *>(s_abort) = 1;
-            atomicExch(err, 1);
-            return false;
-        }
-    }
-    return true;
-}
-
-// Pipeline without CTA-wide barriers per row: stage s is filled by the TMA (full[s]) and
-// released by the 8 warps once they have read their slots (empty[s]), and thread 0 refills it
-// NS rows ahead after that release; ring buffer b holds v of one row, written by all warps
-// (ring_full[b]) and reused two rows later once all warps have read the row's west and east
-// values (ring_empty[b]).  A warp waits only on rows the others finished a step earlier.
-template <bool DOT>
-__global__ void __launch_bounds__(256, 4) k_mg_sweep(const __grid_constant__ CUtensorMap mr,
-                                                  const __grid_constant__ CUtensorMap mc,
-                                                  const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
-                                                  int rows, const float *__restrict__ r,
-                                                  const float *__restrict__ zc, float *__restrict__ out,
-                                                  float2 *part, int *err) {
-    extern __shared__ unsigned char mg_sw_raw[];
-    __shared__ __align__(8) uint64_t full[SW_NS], empty[SW_NS], ring_full[2], ring_empty[2];
-    __shared__ int s_abort;
-    unsigned char *sm = mg_sw_raw + ((128u - (mg_saddr(mg_sw_raw) & 127u)) & 127u);
-    float *ring = reinterpret_cast<float *>(sm + SW_NS * SW_STAGE);  // [2][SW_NX][TCB]
-    float *pairb = ring + 2 * SW_NX * TCB;                           // [SW_NX][TCB] dot runs
-    const int cg = threadIdx.x & 7, xl = threadIdx.x >> 3, lane = threadIdx.x & 31;
-    const SwGeo g = sw_geo(F, k, rows);
-    const int x = g.xb + xl;
-    const int col = g.c0 + cg * 4;
-    const bool own = xl >= 1 && xl <= SW_NXI && x < F.W && col < k;
-    const int nrow = g.y1 - g.y0 + 2;  // rows y0-1 .. y1
-    const int Wc = C.W, WcHc = C.W * C.H;
-    constexpr uint32_t kBytes = (uint32_t)(SW_OFF_Z + SW_ZX * TCB * 4);
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < SW_NS; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(&full[s])), "r"(1) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(&empty[s])), "r"(8) : "memory");
-        }
-        for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(&ring_full[b])), "r"(8) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(&ring_empty[b])), "r"(8) : "memory");
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
-    }
-    __syncthreads();
-    auto issue = [&](int ri) {
-        const int s = ri % SW_NS;
-        unsigned char *st = sm + s * SW_STAGE;
-        const int y = g.y0 - 1 + ri;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mg_saddr(&full[s])), "r"(kBytes)
-                     : "memory");
-        mg_tma4(st + SW_OFF_R, &mr, &full[s], g.c0, g.xb, y, g.t);
-        mg_tma4(st + SW_OFF_C, &mc, &full[s], 0, g.xb, y, g.t);
-        // coarse row under fine row y: y = -1 (the halo above the mesh) takes the zero-filled row -1
-        mg_tma4(st + SW_OFF_Z, &mz, &full[s], g.c0, (g.xb - 1) / 2, y >= 0 ? y >> 1 : -1, g.t);
-    };
-    int issued = 0;
-    if (threadIdx.x == 0)
-        for (; issued < SW_NS && issued < nrow; ++issued) issue(issued);
-
-    float4 vn = zero4(), vc = zero4(), rc = zero4();
-    float4 cfc = zero4();        // {+-1/d, gE, gS, pad} of the centre row (y - 1), own slot
-    float gwc = 0.f, gsn = 0.f;  // gE of the west slot (row y - 1); gS of row y - 2
-    float run[4] = {0.f, 0.f, 0.f, 0.f};  // r.z over the rows of the current 8-row group
-    bool ok = true;
-    for (int ri = 0; ri < nrow; ++ri) {
-        const int s = ri % SW_NS;
-        if (ok) ok = sw_wait(&full[s], (uint32_t)(ri / SW_NS) & 1u, &s_abort, err);
-        const unsigned char *st = sm + s * SW_STAGE;
-        const float4 cf = *reinterpret_cast<const float4 *>(st + SW_OFF_C + xl * 16);
-        const float gws = xl > 0 ? reinterpret_cast<const float *>(st + SW_OFF_C)[(xl - 1) * 4 + 1] : 0.f;
-        const float4 r4 = *reinterpret_cast<const float4 *>(st + SW_OFF_R + xl * (TCB * 4) + cg * 16);
-        const float4 z4 = *reinterpret_cast<const float4 *>(st + SW_OFF_Z + ((xl + 1) >> 1) * (TCB * 4) + cg * 16);
-        __syncwarp();
-        if (lane == 0) sw_arrive(&empty[s]);  // this warp is done with the stage
-        // refill the stage of row ri - 1 (released by every warp a step ago) with row ri - 1 + NS
-        if (threadIdx.x == 0 && ri >= 1 && issued < nrow && ok) {
-            const int rp = ri - 1;
-            if (sw_wait(&empty[rp % SW_NS], (uint32_t)(rp / SW_NS) & 1u, &s_abort, err) &&
-                !*reinterpret_cast<volatile int *>(&s_abort))
-                issue(issued++);
-            else
-                ok = false;
-        }
-        const float4 v = fma4(kScale, z4, (kOmega * fabsf(cf.x)) * r4);
-        // publish v once every warp has read the row this ring buffer held before
-        const int b = ri & 1;
-        if (ri >= 2 && ok) ok = sw_wait(&ring_empty[b], (uint32_t)((ri - 2) >> 1) & 1u, &s_abort, err);
-        *reinterpret_cast<float4 *>(ring + (b * SW_NX + xl) * TCB + cg * 4) = v;
-        __syncwarp();
-        if (lane == 0) sw_arrive(&ring_full[b]);
-        // row yr = y - 1: G v from registers (north, centre, south) and the ring (west, east)
-        const int yr = g.y0 - 2 + ri;
-        if (ri >= 2) {
-            const int bp = (ri - 1) & 1;
-            if (ok) ok = sw_wait(&ring_full[bp], (uint32_t)((ri - 1) >> 1) & 1u, &s_abort, err);
-            const float *rw = ring + bp * SW_NX * TCB;
-            const float4 vw = xl > 0 ? *reinterpret_cast<const float4 *>(rw + (xl - 1) * TCB + cg * 4) : zero4();
-            const float4 ve = xl < SW_NX - 1 ? *reinterpret_cast<const float4 *>(rw + (xl + 1) * TCB + cg * 4) : zero4();
-            __syncwarp();
-            if (lane == 0) sw_arrive(&ring_empty[bp]);
-            if (own) {
-                float4 q = cfc.w * vc;
-                q = fma4(cfc.y, vc - ve, q);
-                q = fma4(gwc, vc - vw, q);
-                q = fma4(cfc.z, vc - v, q);
-                q = fma4(gsn, vc - vn, q);
-                const int i = (g.t * F.H + yr) * F.W + x;
-                if (cfc.x < 0.f) {  // TSV partners on other tiers: v from global memory
-                    const int J = (g.t * C.H + (yr >> 1)) * Wc + (x >> 1);
-                    const int32_t e1 = F.tsv_ptr[i + 1];
-                    for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
-                        const int j = F.tsv_nbr[e];
-                        const float4 vj = fma4(kScale, f4ld(zc + (int64_t)(J + (j > i ? WcHc : -WcHc)) * k + col),
-                                               (kOmega * fabsf(F.coef[j].x)) * f4ld(r + (int64_t)j * k + col));
-                        q = fma4(F.tsv_g[e], vc - vj, q);
-                    }
-                }
-                // floating node: not in P, z = 0
-                const float4 zo = cfc.x == 0.f ? zero4() : fma4(kOmega * fabsf(cfc.x), rc - q, vc);
-                f4st(out + (int64_t)i * k + col, zo);
-                if constexpr (DOT) {
-                    run[0] = fmaf(rc.x, zo.x, run[0]);
-                    run[1] = fmaf(rc.y, zo.y, run[1]);
-                    run[2] = fmaf(rc.z, zo.z, run[2]);
-                    run[3] = fmaf(rc.w, zo.w, run[3]);
-                }
-            }
-            if constexpr (DOT) {
-                // the last row of an 8-row group: per column, the 30 owned slots' runs summed in a
-                // fixed order in double-float; one partial per (strip, group, tier) and column
-                if ((yr & 7) == 7 || yr == g.y1 - 1) {
-                    *reinterpret_cast<float4 *>(pairb + xl * TCB + cg * 4) =
-                        own ? make_float4(run[0], run[1], run[2], run[3]) : zero4();
-                    run[0] = run[1] = run[2] = run[3] = 0.f;
-                    __syncthreads();
-                    if (threadIdx.x < TCB) {
-                        float2 t = make_float2(pairb[threadIdx.x], 0.f);
-                        for (int xx = 1; xx < SW_NX; ++xx) t = df_plus(t, make_float2(pairb[xx * TCB + threadIdx.x], 0.f));
-                        const int c = g.c0 + threadIdx.x;
-                        const int64_t gi = ((int64_t)g.t * ((F.H + 7) >> 3) + (yr >> 3)) * g.tiles_x + g.tx;
-                        if (c < k) part[gi * k + c] = t;
-                    }
-                    __syncthreads();
-                }
-            }
-        }
-        gsn = cfc.z;
-        cfc = cf;
-        gwc = gws;
-        vn = vc;
-        vc = v;
-        rc = r4;
-    }
-    // after an expired wait, let this CTA's own copies land before the CTA exits
-    __syncthreads();
-    if (threadIdx.x == 0 && s_abort) {
-        for (int ri = (issued > SW_NS ? issued - SW_NS : 0); ri < issued; ++ri)
-            for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(&full[ri % SW_NS], (uint32_t)(ri / SW_NS) & 1u); ++q) {
-            }
-    }
-}
-
 // ---- TMA-tiled CG passes on the finest level ---------------------------------------------
 //
 // A CTA owns 32 x 4 nodes of one tier and 32 RHS columns; the operands that the stencil needs
@@ -639,13 +403,14 @@ __device__ __forceinline__ void bar_init_expect(uint64_t *bar, uint32_t bytes) {
 struct CGeo {
     int x0, y0, t, c0;
 };
-__device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int &tile) {  // column block fastest
+__device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int &tile) {
     const int ncb = (k + TCB - 1) / TCB;
     const int tx = (F.W + CX - 1) / CX, ty = (F.H + CY - 1) / CY;
     CGeo g;
-    int b = blockIdx.x / ncb;
+    const int ntile = tx * ty * F.T;
+    int b = F.cb_outer ? (int)(blockIdx.x % ntile) : (int)(blockIdx.x / ncb);
     tile = b;
-    g.c0 = (blockIdx.x % ncb) * TCB;
+    g.c0 = (F.cb_outer ? (int)(blockIdx.x / ntile) : (int)(blockIdx.x % ncb)) * TCB;
     g.x0 = (b % tx) * CX;
     b /= tx;
     g.y0 = (b % ty) * CY;
@@ -964,9 +729,6 @@ struct MgHier {
     double *msc = nullptr;         // per column: recursive residual, previous alpha [2][k]
     // tiled kernels, per level l: r_l (finer side), coefficients, z_l (coarser side of l - 1)
     std::vector<CUtensorMap> map_r, map_c, map_z;
-    // row-streamed finest prolongation: r_0 and the coefficients by rows of 32 slots, z_1 by
-    // rows of 17 aggregates
-    CUtensorMap sw_r, sw_c, sw_z;
     // tiled CG passes on the finest level: direction (z, p[0], p[1], coefficients; east/south
     // halo) and update (p[0], p[1], coefficients; halo on every side)
     CUtensorMap dmap_z, dmap_p[2], dmap_c, umap_p[2], umap_c;
@@ -979,6 +741,7 @@ struct MgHier {
 static Lvl level_of(const GridDev &d) {
     Lvl l;
     l.T = d.T; l.W = d.W; l.H = d.H; l.n = d.n;
+    l.cb_outer = 0;
     l.coef = reinterpret_cast<const float4 *>(d.coef32);
     l.tsv_ptr = d.tsv_ptr; l.tsv_nbr = d.tsv_nbr; l.tsv_g = d.tsv_g32;
     return l;
@@ -1208,7 +971,6 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
             ER_CUDA(cudaMalloc(&h->z[l], bytes));
         }
         h->part_chunks = std::max(std::max(make_lay(g.n, k).chunks, n_tiles(h->lv[1])), n_ctiles(h->lv[0]));
-        h->part_chunks = std::max(h->part_chunks, sw_groups(h->lv[0]));
         if (h->msc) cudaFree(h->msc);
         ER_CUDA(cudaMalloc(&h->msc, (size_t)2 * k * sizeof(double)));
         ER_CUDA(cudaMalloc(&h->part, (size_t)h->part_chunks * k * sizeof(float2)));
@@ -1229,8 +991,8 @@ struct MgRun {
     int k;
     double tol;
     void *Z;
-    int *err;   // the solve's error word (a bounded wait expired)
-    int rows0;  // rows per CTA of the finest level's restriction and prolongation
+    int *err;      // the solve's error word (a bounded wait expired)
+    int cb_outer;  // launch order of the tiled kernels (Lvl::cb_outer)
 };
 
 
@@ -1262,23 +1024,31 @@ FoldArgs fold_args(const MgRun &m, int64_t chunks) {
 void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     MgHier &h = *m.h;
     const int L = (int)h.lv.size(), k = m.k;
+    auto lv = [&](int l) {  // level l with this solve's launch order
+        Lvl x = h.lv[l];
+        x.cb_outer = m.cb_outer;
+        return x;
+    };
     for (int l = 0; l + 1 < L; ++l) {
         const float *rl = l == 0 ? r0 : h.r[l];
         mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_tile<false, false>, tile_grid(h.lv[l + 1], k),
-                  T_SMEM, h.map_r[l], h.map_c[l], h.map_r[l], h.lv[l], h.lv[l + 1], k, rl, (const float *)nullptr,
+                  T_SMEM, h.map_r[l], h.map_c[l], h.map_r[l], lv(l), lv(l + 1), k, rl, (const float *)nullptr,
                   h.r[l + 1], (float2 *)nullptr, m.err);
     }
     const Lvl &C = h.lv[L - 1];
     mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, cinv_grid(C.n, k), 0, (int)C.n, h.ld_inv, k, (const float *)h.ainv,
               (const float *)h.r[L - 1], h.z[L - 1]);
-    for (int l = L - 2; l >= 1; --l)
-        mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<true, false>, tile_grid(h.lv[l + 1], k), T_SMEM, h.map_r[l],
-                  h.map_c[l], h.map_z[l + 1], h.lv[l], h.lv[l + 1], k, (const float *)h.r[l], (const float *)h.z[l + 1],
-                  h.z[l], (float2 *)nullptr, m.err);
-    // finest level: the row-streamed prolongation and post-sweep, with the partials of r.z
-    mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_sweep<true>, sw_grid(h.lv[0], k, m.rows0), SW_SMEM, h.sw_r, h.sw_c, h.sw_z,
-              h.lv[0], h.lv[1], k, m.rows0, r0, (const float *)h.z[1], h.z[0], h.part, m.err);
-    mg_launch(*m.w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_BETA>, dim3((unsigned)k), 0, fold_args(m, sw_groups(h.lv[0])));
+    for (int l = L - 2; l >= 0; --l) {
+        const float *rl = l == 0 ? r0 : h.r[l];
+        if (l == 0)
+            mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_tile<true, true>, tile_grid(h.lv[1], k), T_SMEM, h.map_r[0],
+                      h.map_c[0], h.map_z[1], lv(0), lv(1), k, rl, (const float *)h.z[1], h.z[0], h.part, m.err);
+        else
+            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<true, false>, tile_grid(h.lv[l + 1], k), T_SMEM, h.map_r[l],
+                      h.map_c[l], h.map_z[l + 1], lv(l), lv(l + 1), k, rl, (const float *)h.z[l + 1], h.z[l],
+                      (float2 *)nullptr, m.err);
+    }
+    mg_launch(*m.w, pf, ER_PASS_OTHER, k_mg_fold<FOLD_BETA>, dim3((unsigned)k), 0, fold_args(m, n_tiles(h.lv[1])));
 }
 
 // one PCG iteration from the current residual w.r[0]: z = M r, beta, p' = z + beta p and
@@ -1290,7 +1060,8 @@ int mg_iterate(const MgRun &m, int cur, Prof *pf) {
     const int k = m.k;
     float *r = (float *)w.r[0];
     vcycle(m, r, pf);
-    const Lvl &L0 = h.lv[0];
+    Lvl L0 = h.lv[0];
+    L0.cb_outer = m.cb_outer;
     const dim3 grid = ctile_grid(L0, k);
     const int64_t nct = n_ctiles(L0);
     mg_launch(w, pf, ER_PASS_A, k_mg_dir_tile, grid, S_SMEM, h.dmap_z, h.dmap_p[cur], h.dmap_c, L0, k,
@@ -1330,12 +1101,6 @@ static er_status mg_prepare(GridDev &g, Workspace &w, MgHier **out) {
             if (ms == ER_OK) ms = mg_map(&h->map_z[l], h->z[l], k, h->lv[l], TCB, TZX, TZY);
             if (ms != ER_OK) return ms;
         }
-        {
-            er_status ms = mg_map(&h->sw_r, w.r[0], k, h->lv[0], TCB, SW_NX, 1);
-            if (ms == ER_OK) ms = mg_map(&h->sw_c, h->lv[0].coef, 4, h->lv[0], 4, SW_NX, 1);
-            if (ms == ER_OK) ms = mg_map(&h->sw_z, h->z[1], k, h->lv[1], TCB, SW_ZX, 1);
-            if (ms != ER_OK) return ms;
-        }
         const Lvl &L0 = h->lv[0];
         er_status ms = mg_map(&h->dmap_z, h->z[0], k, L0, TCB, SPX, SPY);
         for (int b = 0; b < 2 && ms == ER_OK; ++b) {
@@ -1349,7 +1114,7 @@ static er_status mg_prepare(GridDev &g, Workspace &w, MgHier **out) {
         if (!attr.load()) {
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
-            ER_CUDA(cudaFuncSetAttribute(k_mg_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_dir_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
@@ -1360,13 +1125,6 @@ static er_status mg_prepare(GridDev &g, Workspace &w, MgHier **out) {
     return ER_OK;
 }
 
-// rows per CTA of the finest level's restriction and prolongation: opt.tile_rows rounded
-// down to a multiple of 8 (the dot partials are kept per 8-row group), else automatic
-static int mg_rows0(const Lvl &L0, int k, int tile_rows) {
-    if (tile_rows > 0) return std::max(8, tile_rows & ~7);
-    return std::max(8, sw_rows(L0, k));
-}
-
 er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const er_solve_opts &opt,
                         er_solve_stats *stats, std::chrono::steady_clock::time_point t0) {
     const int k = w.k;
@@ -1374,7 +1132,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     MgHier *h = nullptr;
     er_status st = mg_prepare(g, w, &h);
     if (st != ER_OK) return st;
-    MgRun m{&g, &w, h, k, tol, Z, w.ints + w.k + w.til.n_colblk, mg_rows0(h->lv[0], k, opt.tile_rows)};
+    MgRun m{&g, &w, h, k, tol, Z, w.ints + w.k + w.til.n_colblk, opt.block_order == 2 ? 1 : 0};
     Prof pf;
     pf.on = opt.profile != 0;
     const bool use_graph = opt.use_graph && !pf.on;
@@ -1505,7 +1263,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
 // the launches of hundreds of uneven networks with no host thread, host poll or
 // synchronisation between them.  A branch runs exactly the kernels of er_sketch + er_solve
 // (multigrid) + er_reff_map on its network; its iteration loop is a device-side WHILE node:
-// the body runs two CG iterations, then a one-thread control kernel reads the network's
+// the body runs the CG iterations of one poll period, then a one-thread control kernel reads the network's
 // unconverged-column count and error word and either ends the loop (all columns met tol and
 // the accurate residual confirmed it, an error, or maxit) or, through a nested IF node, runs
 // the accurate residual replacement, exactly when the host loop of er_solve would.  Converged
@@ -1572,7 +1330,7 @@ struct BatchNet {
     Workspace *w;
     MgHier *h;
     float *Y, *Z;
-    int rows0;
+    int cb_outer;
 };
 
 // the accurate residual replacement of er_solve's multigrid loop, launched on w.s
@@ -1684,17 +1442,20 @@ er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
         b.g = &g;
         b.Y = reinterpret_cast<float *>(static_cast<char *>(B.yz) + off[c]);
         b.Z = reinterpret_cast<float *>(static_cast<char *>(B.yz) + tot + off[c]);
+        // per network launch order (the autotuner's choice): 2 column blocks outermost
+        b.cb_outer = ((tile_rows && tile_rows[c]) ? tile_rows[c] : opt.block_order) == 2 ? 1 : 0;
         er_status st = get_workspace(&g, k, ER_FP32_REFINE, 0, opt.block_order, &b.w);
         if (st != ER_OK) return st;
         st = fp32_prepare(g, *b.w, b.Y, b.Z);
         if (st != ER_OK) return st;
         st = mg_prepare(g, *b.w, &b.h);
         if (st != ER_OK) return st;
-        b.rows0 = mg_rows0(b.h->lv[0], k, tile_rows ? tile_rows[c] : 0);
         nets.push_back(b);
     }
 
-    const int block = 2;
+    // iterations per loop body: er_solve's poll period, so that every decision falls where the
+    // host loop makes it
+    const int block = std::max(2, opt.check_every + (opt.check_every & 1));
     ER_CUDA(cudaGraphCreate(&B.graph, 0));
     if (nets.empty()) {  // every network was small
         ER_CUDA(cudaStreamSynchronize(us));
@@ -1703,7 +1464,7 @@ er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
     for (BatchNet &b : nets) {
         Workspace &w = *b.w;
         cudaStream_t saved = w.s;
-        MgRun m{b.g, &w, b.h, k, opt.tol, b.Z, w.ints + w.k + w.til.n_colblk, b.rows0};
+        MgRun m{b.g, &w, b.h, k, opt.tol, b.Z, w.ints + w.k + w.til.n_colblk, b.cb_outer};
         MgBatchState *sp = dstate + b.c;
         cudaGraphConditionalHandle h_loop;
         ER_CUDA(cudaGraphConditionalHandleCreate(&h_loop, B.graph, 1, cudaGraphCondAssignDefault));
@@ -1718,7 +1479,7 @@ er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
         cudaGraph_t body = nullptr;
         if (st == ER_OK) st = add_conditional(cs, h_loop, cudaGraphCondTypeWhile, &body);
         if (st == ER_OK) {
-            // loop body: two iterations, the control kernel, and the replacement under an IF node
+            // loop body: `block` iterations, the control kernel, and the replacement under an IF node
             cudaGraphConditionalHandle h_repl;
             ER_CUDA(cudaGraphConditionalHandleCreate(&h_repl, body, 0, cudaGraphCondAssignDefault));
             ER_CUDA(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));

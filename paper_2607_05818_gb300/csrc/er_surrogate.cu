@@ -237,7 +237,10 @@ static er_status backward(er_surrogate *s, const __nv_bfloat16 *maps, int B, cud
         // first conv: input (up(below) | eb[l])
         const __nv_bfloat16 *below = l == L - 2 ? s->eb[L - 1].a : s->db[l + 1].a;
         __nv_bfloat16 *below_g = l == L - 2 ? s->eb[L - 1].g : s->db[l + 1].g;
-        SUR_CUDA(unet_wgrad3x3(wgrad_in(below, cb, 1, s->eb[l].a, c, B, h, w, c1.cout), s->da[l].g, c1.gw, st));
+        // the upsampled path at full resolution (the scratch is free until the data gradient
+        // below), so that the weight gradient's operand boxes can be fetched by the TMA
+        SUR_CUDA(unet_upsample2x(below, s->scratch, B, h, w, cb, st));
+        SUR_CUDA(unet_wgrad3x3(wgrad_in(s->scratch, cb, 0, s->eb[l].a, c, B, h, w, c1.cout), s->da[l].g, c1.gw, st));
         SUR_CUDA(unet_bias_grad(s->da[l].g, c1.gb, M, c1.cout, st));
         SUR_CUDA(unet_conv3x3(dgrad_conv(c1, s->da[l].g, B, h, w, s->scratch, below, cb, 1, s->eb[l].g, s->eb[l].a), st));
         SUR_CUDA(unet_upsample_bwd(s->scratch, below_g, B, h, w, cb, 0, st));

@@ -44,8 +44,12 @@ cudaError_t unet_conv3x3_mma(const UConv &c, cudaStream_t s);
 cudaError_t unet_take_error(int *host, cudaStream_t s);
 // launches of the convolution kernels since the last reset: [0..5] persistent TMA kernel with
 // 32-channel K steps and N tiles of 32, 64, 96, 128, 192, 256; [6..11] the same with 64-channel
-// K steps; [12] cp.async-staged kernel; [13] weight gradient
+// K steps; [12] cp.async-staged kernel; [13] weight gradient on mma.sync; [14] weight gradient
+// on tcgen05
 void unet_conv_counts(int64_t *out, int n, int reset);
+// weight gradient dW += sum_p dY[p][o] X[p + tap][c] (FP32 atomics): on tcgen05 when the output
+// channels are a multiple of 128, the input channels of 64 and the input is at full
+// resolution, else on mma.sync
 cudaError_t unet_wgrad3x3(const UConv &c, const __nv_bfloat16 *dy, float *dw, cudaStream_t s);
 cudaError_t unet_maxpool(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c, cudaStream_t s);
 cudaError_t unet_maxpool_bwd(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int nb, int h, int w,

@@ -729,6 +729,160 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// weight gradient on tcgen05: dW[o][tap][c] += sum over a pixel range of dY[p][o] X[p + tap][c],
+// an MMA with M = 128 output channels, N = bn input channels of one tap and K = pixels.  Both
+// operands are MN-major in memory (the channels of a pixel are contiguous), so the TMA lands
+// 64-pixel boxes of 64 channels (128-byte rows, 128-byte swizzle) and the MMAs read them as
+// MN-major operands: within a 1,024-byte swizzle atom 64 consecutive channels x 8 pixels,
+// atoms of further channels 8 KB apart (leading byte offset), groups of 8 pixels 1 KB apart
+// (stride byte offset).  The box of x is the dY box shifted by the tap, zero-filled outside the
+// image, so the pixel rows of both operands correspond.  One tile per CTA:
+//   warp 0 (one thread)  producer: per K step the M/64 boxes of dY and bn/64 boxes of x
+//   warp 1               allocates bn TMEM columns; one thread issues 4 MMAs (K = 16) per stage
+//   warps 2-5            epilogue: tcgen05.ld of their lane quarter, FP32 atomics into dW
+// (split-K over pixel ranges: the CTAs of one output tile add their sums).  Every wait is
+// bounded in time; on expiry the kernel records *err, stops every role and frees TMEM.
+struct WgTcArgs {
+    float *dw;
+    int cin, c1, cout, bn, tiles_c, blocks_per_split, n_blocks;
+    int nb, h, wd, bx, by, bimg;
+    int stages;
+    int *err;
+};
+
+// MN-major operand descriptor, 128-byte swizzle: channel atoms (64 x 8) `lbo` bytes apart,
+// groups of 8 pixels 1,024 bytes apart, descriptor version 1, swizzle mode 2 (128B)
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr, uint32_t lbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+constexpr int WG_M = 128, WG_KP = 64;  // output channels per tile; pixels per K step
+
+__global__ void __launch_bounds__(192, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap mdy, const __grid_constant__ CUtensorMap mx1,
+               const __grid_constant__ CUtensorMap mx2, const WgTcArgs a) {
+    extern __shared__ unsigned char wg_smem_raw[];
+    constexpr int kMaxStages = 8;
+    __shared__ uint64_t full[kMaxStages], empty[kMaxStages], tfull, mdone;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_s;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(wg_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    constexpr int BOX = WG_KP * 128;          // one 64-channel x 64-pixel box: 8 KB
+    constexpr int ABYTES = (WG_M / 64) * BOX;  // 16 KB
+    const int bbytes = (a.bn / 64) * BOX;
+    const int stg = ABYTES + bbytes;
+    const int S = a.stages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // tile: output channel block, (tap, input channel block), pixel split
+    const int o0 = blockIdx.x * WG_M;
+    const int kk = blockIdx.y / a.tiles_c, c0 = (blockIdx.y % a.tiles_c) * a.bn;
+    const int b0 = blockIdx.z * a.blocks_per_split;
+    const int b1 = min(b0 + a.blocks_per_split, a.n_blocks);
+    const int nkb = b1 - b0;
+    const int64_t HW = (int64_t)a.h * a.wd;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&tfull, 1);
+        mbar_init(&mdone, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(a.bn)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int last[kMaxStages];
+            for (int s = 0; s < kMaxStages; ++s) last[s] = -1;
+            for (int it = 0; it < nkb && !abort_s; ++it) {
+                const int s = it % S;
+                if (!wait_or_abort(&empty[s], (uint32_t)(((it / S) & 1) ^ 1), &abort_s, a.err)) break;
+                unsigned char *st = smem + s * stg;
+                mbar_expect_tx(&full[s], (uint32_t)stg);
+                const int64_t m0 = (int64_t)(b0 + it) * WG_KP;
+                const int img = (int)(m0 / HW);
+                const int y0 = (int)((m0 % HW) / a.wd), x0 = (int)(m0 % a.wd);
+                for (int j = 0; j < WG_M / 64; ++j) tma_box4(st + j * BOX, &mdy, &full[s], o0 + 64 * j, x0, y0, img);
+                const int xs = x0 + kk % 3 - 1, ys = y0 + kk / 3 - 1;
+                for (int j = 0; j < a.bn / 64; ++j) {
+                    const int c = c0 + 64 * j;
+                    if (c < a.c1) tma_box4(st + ABYTES + j * BOX, &mx1, &full[s], c, xs, ys, img);
+                    else tma_box4(st + ABYTES + j * BOX, &mx2, &full[s], c - a.c1, xs, ys, img);
+                }
+                last[s] = it;
+            }
+            for (int s = 0; s < S; ++s)  // every load issued lands before the CTA exits
+                if (last[s] >= 0) {
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_test(&full[s], (uint32_t)((last[s] / S) & 1)) && gtimer() - t0 < kWaitNs) {
+                    }
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::f16, D FP32, A and B BF16, both MN-major (transpose bits 15 and 16)
+            const uint32_t idesc = idesc_bf16_f32(WG_M, a.bn) | (1u << 15) | (1u << 16);
+            bool ok = true;
+            for (int it = 0; it < nkb; ++it) {
+                const int s = it % S;
+                if (!wait_or_abort(&full[s], (uint32_t)((it / S) & 1), &abort_s, a.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ab = saddr(smem + s * stg), bb = ab + ABYTES;
+#pragma unroll
+                for (int k16 = 0; k16 < WG_KP / 16; ++k16)  // 16 pixels = 2 groups of 8 rows = 2 KB
+                    tc_mma(tmem, sdesc_mn_sw128(ab + k16 * 2048, BOX), sdesc_mn_sw128(bb + k16 * 2048, BOX), idesc,
+                           (it | k16) != 0);
+                tc_commit(&empty[s]);
+            }
+            if (ok) tc_commit(&tfull);
+            tc_commit(&mdone);  // all MMAs issued above complete before TMEM is released
+            const unsigned long long t0 = gtimer();
+            while (!mbar_test(&mdone, 0) && gtimer() - t0 < kWaitNs) {
+            }
+        }
+    } else if (nkb > 0) {
+        const int q = warp & 3;  // TMEM lane quarter = output channels o0 + 32q ..
+        if (wait_or_abort(&tfull, 0, &abort_s, a.err)) {
+            tc_fence_after();
+            const int o = o0 + q * 32 + lane;
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+            for (int cc = 0; cc < a.bn; cc += 16) {
+                float v[16];
+                tc_ld16(tbase + (uint32_t)cc, v);
+                if (o < a.cout) {
+                    float *dst = a.dw + ((int64_t)o * 9 + kk) * a.cin + c0 + cc;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) atomicAdd(dst + j, v[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.bn) : "memory");
+    }
+}
+
 // nearest 2x upsampling [n][h/2][w/2][c] -> [n][h][w][c], 16 bytes per thread
 __global__ void k_upsample2x(const __nv_bfloat16 *x, __nv_bfloat16 *y, int nb, int h, int w, int c) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // 8-channel chunk of y
@@ -1293,7 +1447,102 @@ cudaError_t unet_conv3x3_mma(const UConv &c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// pixel box of 64 consecutive pixels: bimg images x by rows x bx columns
+static bool wg_pixel_box(int h, int w, int &bx, int &by, int &bimg) {
+    using unet::WG_KP;
+    if (w >= WG_KP) {
+        if (w % WG_KP) return false;
+        bx = WG_KP, by = 1, bimg = 1;
+        return true;
+    }
+    if (WG_KP % w) return false;
+    bx = w;
+    const int rows = WG_KP / w;
+    if (h >= rows) {
+        if (h % rows) return false;
+        by = rows, bimg = 1;
+        return true;
+    }
+    if (rows % h) return false;
+    by = h, bimg = rows / h;
+    return true;
+}
+
+// the tcgen05 weight gradient; cudaErrorNotSupported for shapes it does not take (output and
+// input channels not multiples of 128 and 64, an input read at half resolution, pixel counts
+// that do not tile into 64-pixel boxes)
+static cudaError_t unet_wgrad3x3_tc(const UConv &c, const __nv_bfloat16 *dy, float *dw, cudaStream_t s) {
+    using namespace unet;
+    const int cin = c.c1 + c.c2;
+    int bx, by, bimg;
+    if (c.x1_half || c.cout % WG_M || c.c1 % 64 || c.c2 % 64 || !wg_pixel_box(c.h, c.w_, bx, by, bimg))
+        return cudaErrorNotSupported;
+    int bn = 0;
+    for (int cand : {256, 128, 64})
+        if (c.c1 % cand == 0 && (c.c2 == 0 || c.c2 % cand == 0)) {
+            bn = cand;
+            break;
+        }
+    if (bn == 0) return cudaErrorNotSupported;
+    const int stg = (WG_M / 64 + bn / 64) * WG_KP * 128;
+    const int stages = std::min(8, (200 * 1024) / stg);
+    constexpr int kMaxDyn = 200 * 1024 + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap mdy, mx1, mx2;
+    const cuuint32_t box[4] = {64, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bimg};
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
+        const cuuint64_t str[3] = {(cuuint64_t)c.cout * 2, (cuuint64_t)c.cout * 2 * c.w_,
+                                   (cuuint64_t)c.cout * 2 * c.w_ * c.h};
+        cudaError_t e = bf16_map(&mdy, dy, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)c.c1, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
+        const cuuint64_t str[3] = {(cuuint64_t)c.c1 * 2, (cuuint64_t)c.c1 * 2 * c.w_, (cuuint64_t)c.c1 * 2 * c.w_ * c.h};
+        cudaError_t e = bf16_map(&mx1, c.x1, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B);
+        if (e != cudaSuccess) return e;
+    }
+    if (c.c2 > 0) {
+        const cuuint64_t dims[4] = {(cuuint64_t)c.c2, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
+        const cuuint64_t str[3] = {(cuuint64_t)c.c2 * 2, (cuuint64_t)c.c2 * 2 * c.w_, (cuuint64_t)c.c2 * 2 * c.w_ * c.h};
+        cudaError_t e = bf16_map(&mx2, c.x2, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B);
+        if (e != cudaSuccess) return e;
+    } else {
+        mx2 = mx1;
+    }
+    WgTcArgs a{};
+    a.dw = dw; a.cin = cin; a.c1 = c.c1; a.cout = c.cout; a.bn = bn; a.tiles_c = cin / bn;
+    a.nb = c.nb; a.h = c.h; a.wd = c.w_; a.bx = bx; a.by = by; a.bimg = bimg;
+    a.stages = stages;
+    a.err = err_word();
+    if (!a.err) return cudaErrorInvalidSymbol;
+    const int64_t M = (int64_t)c.nb * c.h * c.w_;
+    a.n_blocks = (int)((M + WG_KP - 1) / WG_KP);
+    const int tiles = (c.cout / WG_M) * 9 * a.tiles_c;
+    const int nsm = sm_count();
+    if (nsm <= 0) return cudaErrorUnknown;
+    // split the pixels so that the grid covers every SM about twice
+    int splits = std::max(1, std::min(a.n_blocks, (2 * nsm + tiles - 1) / tiles));
+    a.blocks_per_split = (a.n_blocks + splits - 1) / splits;
+    splits = (a.n_blocks + a.blocks_per_split - 1) / a.blocks_per_split;
+    k_wgrad_tc<<<dim3((unsigned)(c.cout / WG_M), (unsigned)(9 * a.tiles_c), (unsigned)splits), 192,
+                 stages * stg + 1024, s>>>(mdy, mx1, mx2, a);
+    const cudaError_t le = cudaGetLastError();
+    if (le == cudaSuccess) g_conv_counts[14].fetch_add(1);
+    return le;
+}
+
 cudaError_t unet_wgrad3x3(const UConv &c, const __nv_bfloat16 *dy, float *dw, cudaStream_t s) {
+    {
+        const cudaError_t e = unet_wgrad3x3_tc(c, dy, dw, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     using namespace unet;
     static bool attr = false;
     const int smem = WSTAGES * WBK * (WBM + WBN) * 2;

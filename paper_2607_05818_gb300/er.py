@@ -471,7 +471,7 @@ def conv3x3_wgrad(x, dy, B, H, W, cin, cout, dw, stream=None) -> None:
 
 
 CONV_COUNT_SLOTS = ([f"tma_k32_n{n}" for n in (32, 64, 96, 128, 192, 256)]
-                    + [f"tma_k64_n{n}" for n in (32, 64, 96, 128, 192, 256)] + ["staged", "wgrad", "-", "-"])
+                    + [f"tma_k64_n{n}" for n in (32, 64, 96, 128, 192, 256)] + ["staged", "wgrad_mma", "wgrad_tc", "-"])
 
 
 def conv_launch_counts(reset=False) -> dict:

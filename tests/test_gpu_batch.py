@@ -112,36 +112,38 @@ def test_multigrid_batch_equals_single_solves(er):
         g.destroy()
 
 
-def test_multigrid_autotuned_rows_are_valid_and_change_only_speed(er, tmp_path, monkeypatch):
-    """The autotuner's choice of the finest prolongation's rows per CTA, per size class, is one
-    of its candidates, and the maps it gives are bitwise those of the library's default, both
-    for er_solve and for the batching form (the dot partials are kept per 8-row group)."""
+def test_multigrid_autotuned_order_is_valid_and_changes_only_speed(er, tmp_path, monkeypatch):
+    """The autotuner's choice of the multigrid kernels' launch order, per size class, is one of
+    its candidates, and the maps it gives are bitwise those of the library's default, both for
+    er_solve and for the batching form."""
     monkeypatch.setenv("ER_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     from paper_2607_05818_gb300 import autotune
     rng = np.random.default_rng(2025)
     nets = [I.batch_candidate(rng, 0, T=2, W=64, n_tsv=60), I.batch_candidate(rng, 1, T=3, W=128, n_tsv=200),
             I.batch_candidate(rng, 2, T=4, W=64, n_tsv=100, clustered=True)]
-    k, seed = 32, 99
-    rows = [autotune.best_mg_rows(n, k) for n in nets]
-    print(f"tuned rows {rows}; timings {autotune._load()}")
-    assert all(r in autotune.CANDIDATE_MG_ROWS for r in rows)
+    k, seed = 64, 99
+    orders = [autotune.best_mg_order(n, k) for n in nets]
+    print(f"tuned orders {orders}; timings {autotune._load()}")
+    assert all(o in autotune.CANDIDATE_MG_ORDERS for o in orders)
     grids = [er.grid_create(n) for n in nets]
     opts = er.default_solve_opts("fp32", precond=1, check_every=2)
     R0 = [torch.empty(n.n, dtype=torch.float64, device="cuda") for n in nets]
     R1 = [torch.empty(n.n, dtype=torch.float64, device="cuda") for n in nets]
+    R2 = [torch.empty(n.n, dtype=torch.float64, device="cuda") for n in nets]
     er.batch_solve(grids, k, seed, R0, opts=opts)
-    er.batch_solve(grids, k, seed, R1, opts=opts, tile_rows=rows)
+    er.batch_solve(grids, k, seed, R1, opts=opts, tile_rows=orders)
+    er.batch_solve(grids, k, seed, R2, opts=opts, tile_rows=[3 - o for o in orders])
     torch.cuda.synchronize()
-    for a, b in zip(R0, R1):
-        assert torch.equal(a, b)
-    # er_solve with every candidate row count: the same map
+    for a, b, c in zip(R0, R1, R2):
+        assert torch.equal(a, b) and torch.equal(a, c)
+    # er_solve with each launch order: the same map
     net, g = nets[1], grids[1]
     Y = torch.empty((net.n, k), dtype=torch.float32, device="cuda")
     er.sketch(g, k, seed, "fp32", Y)
     outs = []
-    for r in autotune.CANDIDATE_MG_ROWS:
+    for o in autotune.CANDIDATE_MG_ORDERS:
         Z = torch.empty_like(Y)
-        er.solve(g, Y, Z, k, "fp32", er.default_solve_opts("fp32", precond=1, check_every=2, tile_rows=r))
+        er.solve(g, Y, Z, k, "fp32", er.default_solve_opts("fp32", precond=1, check_every=2, block_order=o))
         outs.append(Z)
     torch.cuda.synchronize()
     for Z in outs[1:]:

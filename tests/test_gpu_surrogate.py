@@ -135,7 +135,10 @@ DGRAD_CASES = [  # (B, H, W, cin, cout, tile_n, expected); the data gradient has
     (3, 8, 8, 128, 96, 128, ("tma", 128, 32)),
     (2, 24, 24, 256, 64, 256, ("staged", 256, 32)),
 ]
-WGRAD_CASES = [(4, 16, 16, 64, 128), (3, 8, 8, 96, 64), (2, 24, 24, 32, 32), (2, 16, 16, 256, 256)]
+WGRAD_CASES = [  # (B, H, W, cin, cout, expected kernel)
+    (4, 16, 16, 64, 128, "wgrad_tc"), (2, 16, 16, 256, 256, "wgrad_tc"), (20, 32, 32, 128, 256, "wgrad_tc"),
+    (3, 8, 8, 192, 128, "wgrad_tc"), (8, 4, 4, 512, 256, "wgrad_tc"), (2, 64, 64, 64, 128, "wgrad_tc"),
+    (3, 8, 8, 96, 64, "wgrad_mma"), (2, 24, 24, 32, 32, "wgrad_mma")]
 
 
 def _bf16_dev(a):
@@ -192,14 +195,18 @@ def test_conv_layer_dgrad_elementwise(er, B, H, W, cin, cout, tile_n, expect):
     _check_rounded(got, ref, absum, 9 * cout, "dgrad")
 
 
-@pytest.mark.parametrize("B,H,W,cin,cout", WGRAD_CASES)
-def test_conv_layer_wgrad_elementwise(er, B, H, W, cin, cout):
+@pytest.mark.parametrize("B,H,W,cin,cout,kern", WGRAD_CASES)
+def test_conv_layer_wgrad_elementwise(er, B, H, W, cin, cout, kern):
     from oracle.unet_ref import conv3x3_bwd
     rng = np.random.default_rng(B * 3000 + cin + cout)
     x = bf16(rng.normal(0, 1, (B, H, W, cin)))
     dy = bf16(rng.normal(0, 1, (B, H, W, cout)))
     dw = torch.full((cout, 3, 3, cin), float("nan"), dtype=torch.float32, device="cuda")
+    er.conv_launch_counts(reset=True)
     er.conv3x3_wgrad(_bf16_dev(x), _bf16_dev(dy), B, H, W, cin, cout, dw)
+    ran = {k_: v for k_, v in er.conv_launch_counts().items() if v}
+    print(f"wgrad {B}x{H}x{W} {cin}x{cout}: ran {ran}")
+    assert ran == {kern: 1}, ran
     got = dw.cpu().numpy().astype(np.float64)
     w0 = np.zeros((cout, 3, 3, cin))
     ref = conv3x3_bwd(x, w0, dy)[1]
