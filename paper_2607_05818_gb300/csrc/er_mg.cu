@@ -1461,6 +1461,8 @@ er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
         ER_CUDA(cudaStreamSynchronize(us));
     }
     cudaStream_t cs = B.s[0], cs2 = B.s[1], cs3 = B.s[2];
+    // every network is an independent branch (limiting them to 8-64 chains of networks run one
+    // after another measured the same throughput)
     for (BatchNet &b : nets) {
         Workspace &w = *b.w;
         cudaStream_t saved = w.s;

@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(192, 1)
 // bounded in time; on expiry the kernel records *err, stops every role and frees TMEM.
 struct WgTcArgs {
     float *dw;
-    int cin, c1, cout, bn, tiles_c, blocks_per_split, n_blocks;
+    int cin, c1, c2, cout, bn, tiles_c1, tiles_c, blocks_per_split, n_blocks;
     int nb, h, wd, bx, by, bimg;
     int stages;
     int *err;
@@ -776,9 +776,15 @@ __global__ void __launch_bounds__(192, 1)
     const int stg = ABYTES + bbytes;
     const int S = a.stages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // tile: output channel block, (tap, input channel block), pixel split
+    // tile: output channel block, (tap, input channel block of x1 or of x2), pixel split; a
+    // block's channels beyond its source (and output channels beyond cout) are zero-filled by
+    // the TMA and not stored
     const int o0 = blockIdx.x * WG_M;
-    const int kk = blockIdx.y / a.tiles_c, c0 = (blockIdx.y % a.tiles_c) * a.bn;
+    const int kk = blockIdx.y / a.tiles_c, tci = blockIdx.y % a.tiles_c;
+    const bool second = tci >= a.tiles_c1;
+    const int cx = (second ? tci - a.tiles_c1 : tci) * a.bn;  // first channel within its source
+    const int csrc = second ? a.c2 : a.c1;
+    const int cbase = second ? a.c1 + cx : cx;                 // first channel within dW's cin
     const int b0 = blockIdx.z * a.blocks_per_split;
     const int b1 = min(b0 + a.blocks_per_split, a.n_blocks);
     const int nkb = b1 - b0;
@@ -819,11 +825,8 @@ __global__ void __launch_bounds__(192, 1)
                 const int y0 = (int)((m0 % HW) / a.wd), x0 = (int)(m0 % a.wd);
                 for (int j = 0; j < WG_M / 64; ++j) tma_box4(st + j * BOX, &mdy, &full[s], o0 + 64 * j, x0, y0, img);
                 const int xs = x0 + kk % 3 - 1, ys = y0 + kk / 3 - 1;
-                for (int j = 0; j < a.bn / 64; ++j) {
-                    const int c = c0 + 64 * j;
-                    if (c < a.c1) tma_box4(st + ABYTES + j * BOX, &mx1, &full[s], c, xs, ys, img);
-                    else tma_box4(st + ABYTES + j * BOX, &mx2, &full[s], c - a.c1, xs, ys, img);
-                }
+                for (int j = 0; j < a.bn / 64; ++j)
+                    tma_box4(st + ABYTES + j * BOX, second ? &mx2 : &mx1, &full[s], cx + 64 * j, xs, ys, img);
                 last[s] = it;
             }
             for (int s = 0; s < S; ++s)  // every load issued lands before the CTA exits
@@ -868,9 +871,10 @@ __global__ void __launch_bounds__(192, 1)
                 float v[16];
                 tc_ld16(tbase + (uint32_t)cc, v);
                 if (o < a.cout) {
-                    float *dst = a.dw + ((int64_t)o * 9 + kk) * a.cin + c0 + cc;
+                    float *dst = a.dw + ((int64_t)o * 9 + kk) * a.cin + cbase + cc;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) atomicAdd(dst + j, v[j]);
+                    for (int j = 0; j < 16; ++j)
+                        if (cx + cc + j < csrc) atomicAdd(dst + j, v[j]);
                 }
             }
         }
@@ -1468,22 +1472,22 @@ static bool wg_pixel_box(int h, int w, int &bx, int &by, int &bimg) {
     return true;
 }
 
-// the tcgen05 weight gradient; cudaErrorNotSupported for shapes it does not take (output and
-// input channels not multiples of 128 and 64, an input read at half resolution, pixel counts
-// that do not tile into 64-pixel boxes)
+// the tcgen05 weight gradient; cudaErrorNotSupported for shapes it does not take (channel
+// counts not multiples of 32, an input read at half resolution, pixel counts that do not tile
+// into 64-pixel boxes).  Channel blocks of 64 whose channels run past their tensor (layers of
+// 32 or 96 channels) are zero-filled and their extra rows and columns are not stored.
 static cudaError_t unet_wgrad3x3_tc(const UConv &c, const __nv_bfloat16 *dy, float *dw, cudaStream_t s) {
     using namespace unet;
     const int cin = c.c1 + c.c2;
     int bx, by, bimg;
-    if (c.x1_half || c.cout % WG_M || c.c1 % 64 || c.c2 % 64 || !wg_pixel_box(c.h, c.w_, bx, by, bimg))
+    if (c.x1_half || c.cout % 32 || c.c1 % 32 || c.c2 % 32 || c.c1 == 0 || !wg_pixel_box(c.h, c.w_, bx, by, bimg))
         return cudaErrorNotSupported;
-    int bn = 0;
-    for (int cand : {256, 128, 64})
-        if (c.c1 % cand == 0 && (c.c2 == 0 || c.c2 % cand == 0)) {
+    int bn = 64;
+    for (int cand : {256, 128})
+        if (c.c1 % cand == 0 && c.c2 % cand == 0) {
             bn = cand;
             break;
         }
-    if (bn == 0) return cudaErrorNotSupported;
     const int stg = (WG_M / 64 + bn / 64) * WG_KP * 128;
     const int stages = std::min(8, (200 * 1024) / stg);
     constexpr int kMaxDyn = 200 * 1024 + 1024;
@@ -1499,39 +1503,42 @@ static cudaError_t unet_wgrad3x3_tc(const UConv &c, const __nv_bfloat16 *dy, flo
         const cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
         const cuuint64_t str[3] = {(cuuint64_t)c.cout * 2, (cuuint64_t)c.cout * 2 * c.w_,
                                    (cuuint64_t)c.cout * 2 * c.w_ * c.h};
-        cudaError_t e = bf16_map(&mdy, dy, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B);
-        if (e != cudaSuccess) return e;
+        if (bf16_map(&mdy, dy, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B) != cudaSuccess)
+            return cudaErrorNotSupported;
     }
     {
         const cuuint64_t dims[4] = {(cuuint64_t)c.c1, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
         const cuuint64_t str[3] = {(cuuint64_t)c.c1 * 2, (cuuint64_t)c.c1 * 2 * c.w_, (cuuint64_t)c.c1 * 2 * c.w_ * c.h};
-        cudaError_t e = bf16_map(&mx1, c.x1, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B);
-        if (e != cudaSuccess) return e;
+        if (bf16_map(&mx1, c.x1, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B) != cudaSuccess)
+            return cudaErrorNotSupported;
     }
     if (c.c2 > 0) {
         const cuuint64_t dims[4] = {(cuuint64_t)c.c2, (cuuint64_t)c.w_, (cuuint64_t)c.h, (cuuint64_t)c.nb};
         const cuuint64_t str[3] = {(cuuint64_t)c.c2 * 2, (cuuint64_t)c.c2 * 2 * c.w_, (cuuint64_t)c.c2 * 2 * c.w_ * c.h};
-        cudaError_t e = bf16_map(&mx2, c.x2, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B);
-        if (e != cudaSuccess) return e;
+        if (bf16_map(&mx2, c.x2, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_128B) != cudaSuccess)
+            return cudaErrorNotSupported;
     } else {
         mx2 = mx1;
     }
     WgTcArgs a{};
-    a.dw = dw; a.cin = cin; a.c1 = c.c1; a.cout = c.cout; a.bn = bn; a.tiles_c = cin / bn;
+    a.dw = dw; a.cin = cin; a.c1 = c.c1; a.c2 = c.c2; a.cout = c.cout; a.bn = bn;
+    a.tiles_c1 = (c.c1 + bn - 1) / bn;
+    a.tiles_c = a.tiles_c1 + (c.c2 + bn - 1) / bn;
     a.nb = c.nb; a.h = c.h; a.wd = c.w_; a.bx = bx; a.by = by; a.bimg = bimg;
     a.stages = stages;
     a.err = err_word();
     if (!a.err) return cudaErrorInvalidSymbol;
     const int64_t M = (int64_t)c.nb * c.h * c.w_;
     a.n_blocks = (int)((M + WG_KP - 1) / WG_KP);
-    const int tiles = (c.cout / WG_M) * 9 * a.tiles_c;
+    const int tiles_o = (c.cout + WG_M - 1) / WG_M;
+    const int tiles = tiles_o * 9 * a.tiles_c;
     const int nsm = sm_count();
     if (nsm <= 0) return cudaErrorUnknown;
     // split the pixels so that the grid covers every SM about twice
     int splits = std::max(1, std::min(a.n_blocks, (2 * nsm + tiles - 1) / tiles));
     a.blocks_per_split = (a.n_blocks + splits - 1) / splits;
     splits = (a.n_blocks + a.blocks_per_split - 1) / a.blocks_per_split;
-    k_wgrad_tc<<<dim3((unsigned)(c.cout / WG_M), (unsigned)(9 * a.tiles_c), (unsigned)splits), 192,
+    k_wgrad_tc<<<dim3((unsigned)tiles_o, (unsigned)(9 * a.tiles_c), (unsigned)splits), 192,
                  stages * stg + 1024, s>>>(mdy, mx1, mx2, a);
     const cudaError_t le = cudaGetLastError();
     if (le == cudaSuccess) g_conv_counts[14].fetch_add(1);

@@ -138,7 +138,10 @@ DGRAD_CASES = [  # (B, H, W, cin, cout, tile_n, expected); the data gradient has
 WGRAD_CASES = [  # (B, H, W, cin, cout, expected kernel)
     (4, 16, 16, 64, 128, "wgrad_tc"), (2, 16, 16, 256, 256, "wgrad_tc"), (20, 32, 32, 128, 256, "wgrad_tc"),
     (3, 8, 8, 192, 128, "wgrad_tc"), (8, 4, 4, 512, 256, "wgrad_tc"), (2, 64, 64, 64, 128, "wgrad_tc"),
-    (3, 8, 8, 96, 64, "wgrad_mma"), (2, 24, 24, 32, 32, "wgrad_mma")]
+    (3, 8, 8, 96, 64, "wgrad_tc"),      # a half-empty 64-channel block of input channels
+    (2, 16, 16, 32, 32, "wgrad_tc"),    # 32 output channels: rows 32-127 of the tile are zero-filled
+    (2, 32, 32, 32, 64, "wgrad_tc"),
+    (2, 24, 24, 32, 32, "wgrad_mma")]   # 24 x 24 does not tile into 64-pixel boxes
 
 
 def _bf16_dev(a):
