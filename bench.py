@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--sur-screen", type=int, default=4096, help="surrogate workload: screened candidates")
     p.add_argument("--sur-k", type=int, default=64, help="surrogate workload: JL columns of labels and verification")
     p.add_argument("--sur-epochs", type=int, default=12)
+    p.add_argument("--sur-batch", type=int, default=128, help="surrogate workloads: candidates per forward call")
     p.add_argument("--sur-recall", type=int, default=512, help="surrogate workload: candidates solved exactly "
                                                                 "to measure the screen's recall (untimed)")
     p.add_argument("--workers", type=int, default=8, help="spawned processes encoding candidate maps")
@@ -394,8 +395,7 @@ def run_batch(args, rank, world, local_rank):
         "sequential": {"value": seq_value, "unit": UNIT, "ms": seq_ms,
                        "note": "er_sketch + er_solve + er_reff_map per candidate, warm workspace, Jacobi"},
         "sequential_multigrid": {"value": seq_mg_value, "unit": UNIT, "ms": seq_mg_ms,
-                                 "note": "as sequential, with the multigrid preconditioner (not available in "
-                                         "the batching form)"},
+                                 "note": "as sequential, with the multigrid preconditioner"},
         "batched_over_sequential": value / seq_value,
         "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk.summary(),
     }
@@ -440,7 +440,7 @@ def run_surrogate(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     del tgt, msk, maps_tr
-    nb = 32
+    nb = args.sur_batch  # candidates per forward call: enough pixel tiles to fill the SMs at the deep levels
     pred = torch.empty((args.sur_screen, W, W, T), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     fwd_launches = 6 * L - 3  # 2L convolutions, L-1 pools, L-1 upsamplings, 2(L-1) decoder convolutions, head
@@ -682,14 +682,14 @@ def run_pairs(args, rank, world, local_rank):
 def run_unet_forward(args, rank, world, local_rank):
     """The surrogate's forward alone: the 6-level, 32-base-channel BF16 U-Net (random He
     weights; the arithmetic does not depend on them) over --sur-screen random 4x256x256
-    candidate maps in batches of 32, timed with CUDA events.  Isolates the tcgen05 convolution
+    candidate maps in batches of --sur-batch (128), timed with CUDA events.  Isolates the tcgen05 convolution
     kernels from training and verification."""
     import torch
     from paper_2607_05818_gb300 import er
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    T, W, L, C, in_ch, nb = 4, 256, 6, 32, 32, 32
+    T, W, L, C, in_ch, nb = 4, 256, 6, 32, 32, args.sur_batch
     model = er.Surrogate(in_ch=in_ch, out_ch=T, levels=L, base=C, H=W, W=W, seed=3 + rank)
     gen = torch.Generator(device=dev)
     gen.manual_seed(11 + rank)
