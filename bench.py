@@ -291,9 +291,10 @@ def ncu_traffic(kernel, workload):
 
 def run_batch(args, rank, world, local_rank):
     """Batching form: 512 TSV-placement candidates (k = 64) through er_batch_solve, with the
-    multigrid preconditioner (one CUDA graph of all networks' solves; the default, --precond mg) or
-    Jacobi (shared launches), the other mode timed once beside it, against the same
-    candidates solved one after another (er_solve per candidate, warm workspace)."""
+    multigrid preconditioner (every pass one persistent launch over all running networks, the
+    loop a device-side graph node; the default, --precond mg) or Jacobi (shared launches), the
+    other mode timed once beside it, against the same candidates solved one after another
+    (er_solve per candidate, warm workspace)."""
     import torch
     from paper_2607_05818_gb300 import er
     from paper_2607_05818_gb300 import instances as I
@@ -386,7 +387,7 @@ def run_batch(args, rank, world, local_rank):
                                     f"{sorted(set(rows))}, {t_tune:.1f} s to tune, untimed)" if rows
                                     else "library default"),
                    "max_rel_residual": last["max_rel_residual"],
-                   "mode": "multigrid: one CUDA graph, each network's loop a device-side conditional node"
+                   "mode": "multigrid: every pass one persistent launch over the running networks, loop in a device-side graph node"
                    if use_mg else "Jacobi: shared launches over a (network, tile) work list"},
         "other_mode": {"mode": "Jacobi shared launches" if use_mg else "multigrid graph of all networks",
                        "value": n_ok / other_s, "unit": UNIT, "seconds": other_s,

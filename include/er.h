@@ -238,8 +238,8 @@ typedef struct {
     double max_rel_residual;  /* final accurate residual, max over all networks and columns */
     double seconds;           /* host wall time of the call */
     int32_t launches;         /* kernels launched */
-    int32_t graph_captures;   /* CUDA graphs captured (one per change of the work list; 0 in the
-                                 multigrid mode, whose solves capture their own graphs) */
+    int32_t graph_captures;   /* CUDA graphs captured (Jacobi: one per change of the work list;
+                                 multigrid: one per group of up to 1,024 networks) */
 } er_batch_stats;
 
 /* Batching form: the all-node R maps of n networks (e.g. TSV-placement candidates of
@@ -251,14 +251,17 @@ typedef struct {
  *     graph per poll period; networks leave the work list as they converge.  tile_rows[c]
  *     (nullable) overrides the y rows swept per CTA for network c (the autotuner's choice).
  *     Workspace is allocated for the call and freed before it returns.
- *   opts->precond == 1 (multigrid): every network's er_sketch + er_solve (multigrid V-cycle)
- *     + er_reff_map, with exactly those kernels, is one branch of a single CUDA graph launched
- *     once, so the launches of all networks interleave on the GPU with no host polling: each
- *     branch's iteration loop is a device-side conditional (WHILE) node whose control kernel
- *     ends it when the network's columns meet tol (the accurate residual replacement runs under
- *     a nested IF node exactly when er_solve's host loop would run it), so converged networks
- *     leave the GPU while the others continue.  Each map equals the single-network map
- *     bitwise.  Networks of at most 512 nodes (their own coarsest level) are solved first
+ *   opts->precond == 1 (multigrid): er_solve's multigrid iteration on all networks at once.
+ *     Every pass (each level's restriction and prolongation, the coarsest solves, direction,
+ *     update, the per-column folds, the accurate residual replacement) is ONE persistent
+ *     launch over the blocks of the networks still running, found through a device-side work
+ *     list; one poll period (opts->check_every iterations) is the body of a device-side WHILE
+ *     node of a CUDA graph launched once per group of up to 1,024 networks, whose last kernel
+ *     takes each network's decisions exactly where er_solve's host loop would (replace, stop)
+ *     and rebuilds the work list, so converged networks leave while the others continue and
+ *     no host thread polls.  Every block runs the single-network kernel's body, so each map
+ *     equals the single-network map (er_sketch + er_solve + er_reff_map) bitwise.  Networks
+ *     of at most 512 nodes (their own coarsest level) are solved first
  *     with er_solve's Jacobi path, as alone.  A grid may appear only once
  *     (ER_ERR_INVALID_ARG otherwise).  tile_rows[c] (nullable) is network c's launch order
  *     as er_solve_opts.block_order (the autotuner's choice per size class; 0 = opts'); it

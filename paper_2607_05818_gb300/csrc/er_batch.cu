@@ -1,6 +1,6 @@
 // Batching form: the all-node R map of many uneven networks, in shared launches
-// (Jacobi, precond 0; below) or as one CUDA graph of multigrid solves (precond 1;
-// mg_batch_graph in er_mg.cu).
+// (Jacobi, precond 0; below) or as persistent level-synchronous multigrid launches under a
+// device-side graph loop (precond 1; mg_batch_solve in er_mg.cu).
 //
 // Every network keeps its own grid (coefficients, TSV CSR), its own vectors and its own
 // per-column CG scalars, but each pass (A, B/B0, accurate residual, initialisation,
@@ -58,7 +58,7 @@ static er_status batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64
             if (grids[d] == grids[c]) return fail(ER_ERR_INVALID_ARG, "a grid appears twice (precond 1 solves networks concurrently)");
     }
     ER_CUDA(cudaSetDevice(dev));
-    if (opt.precond == 1) return mg_batch_graph(grids, n, k, seed, tile_rows, R_out, opt, stats, us, t0);
+    if (opt.precond == 1) return mg_batch_solve(grids, n, k, seed, tile_rows, R_out, opt, stats, us, t0);
     cudaStream_t s = nullptr;
     ER_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct StreamGuard {

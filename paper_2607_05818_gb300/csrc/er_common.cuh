@@ -300,9 +300,13 @@ struct BatchItem {
     const float *b;
 };
 
-// er_fp32.cu: batched passes (mode = MODE_*) over a work list of (network, block)
+// er_fp32.cu: batched passes (mode = MODE_*) over a work list of (network, block); with `sel`,
+// only the networks c with sel[c] != 0 (device array) run
 er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, int n_work, int cur, int rmode,
-                          cudaStream_t s);
+                          cudaStream_t s, const int *sel = nullptr);
+// one network's batch item over its own solve workspace: the arguments and tensor maps of
+// fp32_init / fp32_accum / fp32_residual / fp32_final on (g, w) for the batched passes
+er_status fp32_workspace_item(const GridDev &g, Workspace &w, const void *Yt, void *Z, double tol, BatchItem *it);
 er_status fp32_make_map(CUtensorMap *m, bool f64, const void *base, int64_t d0, int box0, const GridDev &g);
 
 // er_pcg.cu: argument checks and the solve loop on a prepared workspace
@@ -324,9 +328,9 @@ er_status solve_locked(er_grid *g, const void *Yt, void *Z, int32_t k, er_precis
                        er_solve_stats *stats, cudaStream_t us);
 // the grid's cached solve workspace for (k, precision, tiling), allocated on first use
 er_status get_workspace(GridDev *g, int k, er_precision prec, int rows, int order, Workspace **out);
-// the multigrid batching form: every network's sketch, multigrid solve and map in one CUDA
-// graph, each network's iteration loop a device-side conditional (er_mg.cu)
-er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, const int32_t *tile_rows,
+// the multigrid batching form: every pass of er_solve's multigrid iteration one persistent
+// launch over all running networks, each poll period the body of a device-side WHILE node (er_mg.cu)
+er_status mg_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, const int32_t *tile_rows,
                          double *const *R_out, const er_solve_opts &opt, er_batch_stats *stats, cudaStream_t us,
                          std::chrono::steady_clock::time_point t0);
 void fp32_init(const GridDev &g, Workspace &w, const void *Yt, void *Z, double tol, Prof *pf);

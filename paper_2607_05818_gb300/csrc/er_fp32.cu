@@ -559,7 +559,8 @@ __global__ void __launch_bounds__(kThreads) k_fp32_stream(const KArgs<float, flo
 // ---------------------------------------------------------------------------------------
 // batching form: one launch per pass covers the tiles of many networks.  The work list
 // holds (network, block-within-network); each CTA copies its network's arguments into
-// shared memory and runs the same pass as the single-network kernels.
+// shared memory and runs the same pass as the single-network kernels.  With `sel`, only the
+// networks c with sel[c] != 0 run (the other CTAs return at once).
 
 template <int MODE>
 __device__ __forceinline__ void batch_args(const BatchItem &it, int cur, int rmode, KArgs<float, float> &a) {
@@ -580,10 +581,12 @@ __device__ __forceinline__ void batch_args(const BatchItem &it, int cur, int rmo
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3)
-    k_tma_batch(const BatchItem *__restrict__ items, const int2 *__restrict__ work, int cur, int rmode) {
+    k_tma_batch(const BatchItem *__restrict__ items, const int2 *__restrict__ work, int cur, int rmode,
+                const int *__restrict__ sel) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ KArgs<float, float> s_a;
     const int2 wk = work[blockIdx.x];
+    if (sel && !sel[wk.x]) return;
     const BatchItem &it = items[wk.x];
     if (threadIdx.x == 0) batch_args<MODE>(it, cur, rmode, s_a);
     __syncthreads();
@@ -595,9 +598,10 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_A_DOT ? 4 : 3)
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_stream_batch(const BatchItem *__restrict__ items,
-                                                           const int2 *__restrict__ work) {
+                                                           const int2 *__restrict__ work, const int *__restrict__ sel) {
     __shared__ KArgs<float, float> s_a;
     const int2 wk = work[blockIdx.x];
+    if (sel && !sel[wk.x]) return;
     if (threadIdx.x == 0) batch_args<MODE>(items[wk.x], 0, 0, s_a);
     __syncthreads();
     fp32_stream_pass<MODE>(s_a, wk.y);
@@ -643,7 +647,7 @@ static std::atomic<bool> g_attr_done{false};  // set once; solves may run on sev
 static std::atomic<bool> g_battr_done{false};
 
 er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, int n_work, int cur, int rmode,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int *sel) {
     if (!g_battr_done.load()) {
         ER_CUDA(cudaFuncSetAttribute(k_tma_batch<MODE_A_DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      dyn_smem<MODE_A_DOT>()));
@@ -658,13 +662,13 @@ er_status fp32_batch_pass(int mode, const BatchItem *items, const int2 *work, in
     if (n_work <= 0) return ER_OK;
     const unsigned nb = (unsigned)n_work;
     switch (mode) {
-        case MODE_A_DOT: k_tma_batch<MODE_A_DOT><<<nb, kThreads, dyn_smem<MODE_A_DOT>(), s>>>(items, work, cur, rmode); break;
-        case MODE_B: k_tma_batch<MODE_B><<<nb, kThreads, dyn_smem<MODE_B>(), s>>>(items, work, cur, rmode); break;
-        case MODE_B0: k_tma_batch<MODE_B0><<<nb, kThreads, dyn_smem<MODE_B0>(), s>>>(items, work, cur, rmode); break;
-        case MODE_R: k_tma_batch<MODE_R><<<nb, kThreads, dyn_smem<MODE_R>(), s>>>(items, work, cur, rmode); break;
-        case MODE_INIT: k_stream_batch<MODE_INIT><<<nb, kThreads, 0, s>>>(items, work); break;
-        case MODE_ACCUM: k_stream_batch<MODE_ACCUM><<<nb, kThreads, 0, s>>>(items, work); break;
-        case MODE_UNSCALE: k_stream_batch<MODE_UNSCALE><<<nb, kThreads, 0, s>>>(items, work); break;
+        case MODE_A_DOT: k_tma_batch<MODE_A_DOT><<<nb, kThreads, dyn_smem<MODE_A_DOT>(), s>>>(items, work, cur, rmode, sel); break;
+        case MODE_B: k_tma_batch<MODE_B><<<nb, kThreads, dyn_smem<MODE_B>(), s>>>(items, work, cur, rmode, sel); break;
+        case MODE_B0: k_tma_batch<MODE_B0><<<nb, kThreads, dyn_smem<MODE_B0>(), s>>>(items, work, cur, rmode, sel); break;
+        case MODE_R: k_tma_batch<MODE_R><<<nb, kThreads, dyn_smem<MODE_R>(), s>>>(items, work, cur, rmode, sel); break;
+        case MODE_INIT: k_stream_batch<MODE_INIT><<<nb, kThreads, 0, s>>>(items, work, sel); break;
+        case MODE_ACCUM: k_stream_batch<MODE_ACCUM><<<nb, kThreads, 0, s>>>(items, work, sel); break;
+        case MODE_UNSCALE: k_stream_batch<MODE_UNSCALE><<<nb, kThreads, 0, s>>>(items, work, sel); break;
         default: return fail(ER_ERR_INVALID_ARG, "bad batch pass");
     }
     ER_CUDA(cudaGetLastError());
@@ -719,6 +723,29 @@ static void launch_stream(const KArgs<float, float> &a, Workspace &w, Prof *pf, 
     prof_begin(w, pf, kind);
     k_fp32_stream<MODE><<<(unsigned)w.til.n_ctas(), kThreads, 0, w.s>>>(a);
     prof_end(w, pf, kind);
+}
+
+er_status fp32_workspace_item(const GridDev &g, Workspace &w, const void *Yt, void *Z, double tol, BatchItem *it) {
+    er_status st = fp32_prepare(g, w, Yt, Z);
+    if (st != ER_OK) return st;
+    std::memset(it, 0, sizeof(*it));
+    it->tm[0] = w.tm_r[0];
+    it->tm[1] = w.tm_r[1];
+    it->tm[2] = w.tm_p[0];
+    it->tm[3] = w.tm_p[1];
+    it->tm[4] = w.tm_c;
+    it->tm[5] = w.tm_xhl;
+    it->tm[6] = w.tm_b;
+    it->tm[7] = w.tm_coef;
+    it->a = base_args<float, float>(g, w, tol);
+    for (int i = 0; i < 2; ++i) {
+        it->r[i] = (float *)w.r[i];
+        it->p[i] = (float *)w.p[i];
+    }
+    it->c = (float *)Z;
+    it->xhl = w.xhl;
+    it->b = (const float *)Yt;
+    return ER_OK;
 }
 
 void fp32_init(const GridDev &g, Workspace &w, const void *Yt, void *Z, double tol, Prof *pf) {

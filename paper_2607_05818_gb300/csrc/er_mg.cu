@@ -146,23 +146,30 @@ __device__ __forceinline__ bool mg_try_wait(uint64_t *b, uint32_t parity) {
 }
 
 // Issue the tile's loads and wait for them.  Returns false (error word raised) on expiry.
-__device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, const CUtensorMap *mr,
-                                          const CUtensorMap *mc, const CUtensorMap *mz, int c0, int X0, int Y0, int t,
-                                          int *err) {
+// `init`: the barrier is initialised here (one tile per CTA); otherwise the caller initialised
+// it once and `parity` is the phase this tile completes (a CTA looping over tiles).  The
+// issuing thread runs `hook` while the copies are in flight.
+template <class Hook>
+__device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, uint32_t parity, bool init,
+                                          const CUtensorMap *mr, const CUtensorMap *mc, const CUtensorMap *mz, int c0,
+                                          int X0, int Y0, int t, int *err, const Hook &hook) {
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (init) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
         const uint32_t bytes = (uint32_t)(T_R + TFY * TFX * 16 + (mz ? T_Z : 0));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mg_saddr(bar)), "r"(bytes)
                      : "memory");
         mg_tma4(sm, mr, bar, c0, 2 * X0 - 1, 2 * Y0 - 1, t);
         mg_tma4(sm + T_R, mc, bar, 0, 2 * X0 - 1, 2 * Y0 - 1, t);
         if (mz) mg_tma4(sm + T_R + T_C, mz, bar, c0, X0 - 1, Y0 - 1, t);
+        hook();
     }
     __syncthreads();
     // every thread waits (bounded); the vote makes the outcome uniform across the CTA
     bool done = true;
-    for (uint32_t spins = 0; !mg_try_wait(bar, 0);) {
+    for (uint32_t spins = 0; !mg_try_wait(bar, parity);) {
         if (++spins > kTileSpin) {
             done = false;
             break;
@@ -171,7 +178,7 @@ __device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, cons
     if (__syncthreads_and(done ? 1 : 0)) return true;
     if (threadIdx.x == 0) {  // raise the error word and let this CTA's own copies land first
         atomicExch(err, 1);
-        for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar, 0); ++q) {
+        for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar, parity); ++q) {
         }
     }
     return false;
@@ -184,14 +191,14 @@ struct TileGeo {
 // Block -> (tile, column block).  The column blocks of one tile are adjacent in launch order, so
 // the CTAs that read the same node rows (each takes a 128-byte slice of them) run together and
 // the L2's 256-byte fills are used by both neighbours.
-__device__ __forceinline__ TileGeo tile_geo(const Lvl &C, int k, int &tile) {
+__device__ __forceinline__ TileGeo tile_geo(const Lvl &C, int k, int blk, int &tile) {
     const int ncb = (k + TCB - 1) / TCB;
     const int tx = (C.W + TAX - 1) / TAX, ty = (C.H + TAY - 1) / TAY;
     TileGeo g;
     const int ntile = tx * ty * C.T;
-    int b = C.cb_outer ? (int)(blockIdx.x % ntile) : (int)(blockIdx.x / ncb);
+    int b = C.cb_outer ? blk % ntile : blk / ncb;
     tile = b;
-    g.c0 = (C.cb_outer ? (int)(blockIdx.x / ntile) : (int)(blockIdx.x % ncb)) * TCB;
+    g.c0 = (C.cb_outer ? blk / ntile : blk % ncb) * TCB;
     g.X0 = (b % tx) * TAX;
     b /= tx;
     g.Y0 = (b % ty) * TAY;
@@ -244,23 +251,36 @@ __device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int
     cta_col_partials(r2, k, c0, tile, part);
 }
 
-// prolongation + post-sweep (UP) or pre-sweep + restriction (!UP) over one tile
-template <bool UP, bool DOT>
-__global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUtensorMap mr,
-                                                 const __grid_constant__ CUtensorMap mc,
-                                                 const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
-                                                 const float *__restrict__ r, const float *__restrict__ zc,
-                                                 float *__restrict__ out, float2 *part, int *err) {
-    extern __shared__ unsigned char mg_tile_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    unsigned char *sm = mg_tile_raw + ((128u - (mg_saddr(mg_tile_raw) & 127u)) & 127u);
+// The arrays of one tile pass: finer level F, coarser level C, the finer level's residual r,
+// the coarse correction zc (UP), the output (UP: z of F; !UP: the restricted residual of C),
+// the dot partials (UP with DOT) and the error word.
+struct TileArgs {
+    Lvl F, C;
+    const float *r, *zc;
+    float *out;
+    float2 *part;
+    int *err;
+};
+
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
+// prolongation + post-sweep (UP) or pre-sweep + restriction (!UP) over tile block `blk` of the
+// level pair (ta.F, ta.C); false if the wait on the tile's loads expired (error word raised).
+// `ta` may live in shared memory (read where used) or be built from kernel parameters.
+template <bool UP, bool DOT, class TA, class Hook>
+__device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, uint32_t parity, bool init, int blk,
+                                             const CUtensorMap *mr, const CUtensorMap *mc, const CUtensorMap *mz,
+                                             const TA &ta, int k, const Hook &hook) {
+    const Lvl &F = ta.F, &C = ta.C;
     const float *rs = reinterpret_cast<const float *>(sm);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + T_R);
     const float *zs = reinterpret_cast<const float *>(sm + T_R + T_C);
     int tile;
-    const TileGeo g = tile_geo(C, k, tile);
-    const bool ok = tile_load(sm, &bar, &mr, &mc, UP ? &mz : nullptr, g.c0, g.X0, g.Y0, g.t, err);
-    if (!ok) return;
+    const TileGeo g = tile_geo(C, k, blk, tile);
+    const bool ok = tile_load(sm, bar, parity, init, mr, mc, UP ? mz : nullptr, g.c0, g.X0, g.Y0, g.t, ta.err, hook);
+    if (!ok) return false;
     const int Wc = C.W, WcHc = C.W * C.H;
     float run[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
@@ -284,8 +304,8 @@ __global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUte
         };
         auto gval = [&](int j, int dJ) {  // TSV partner on another tier (global memory)
             const float4 cj = F.coef[j];
-            float4 v = (kOmega * fabsf(cj.x)) * f4ld(r + (int64_t)j * k + col);
-            if constexpr (UP) v = fma4(kScale, f4ld(zc + (int64_t)(J + dJ) * k + col), v);
+            float4 v = (kOmega * fabsf(cj.x)) * f4ld(ta.r + (int64_t)j * k + col);
+            if constexpr (UP) v = fma4(kScale, f4ld(ta.zc + (int64_t)(J + dJ) * k + col), v);
             return v;
         };
         float4 acc = zero4();
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUte
                 const float4 c = cs[ly * TFX + lx];
                 const int i = (g.t * F.H + y) * F.W + x;
                 if (c.x == 0.f) {  // floating node: not in P, z = 0
-                    if constexpr (UP) f4st(out + (int64_t)i * k + col, zero4());
+                    if constexpr (UP) f4st(ta.out + (int64_t)i * k + col, zero4());
                     continue;
                 }
                 const float4 ri = *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
@@ -333,7 +353,7 @@ __global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUte
                 }
                 if constexpr (UP) {
                     const float4 zo = fma4(kOmega * fabsf(c.x), ri - gv, vi);
-                    f4st(out + (int64_t)i * k + col, zo);
+                    f4st(ta.out + (int64_t)i * k + col, zo);
                     if constexpr (DOT) {
                         run[h][0] = fmaf(ri.x, zo.x, run[h][0]);
                         run[h][1] = fmaf(ri.y, zo.y, run[h][1]);
@@ -344,14 +364,28 @@ __global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUte
                     acc = acc + (ri - gv);
                 }
             }
-        if constexpr (!UP) f4st(out + (int64_t)J * k + col, acc);
+        if constexpr (!UP) f4st(ta.out + (int64_t)J * k + col, acc);
     }
     if constexpr (DOT) {
         // per column: the 64 items of the tile that share it (two per thread), summed in a fixed order
         const float2 r2[4] = {mg_two_sum(run[0][0], run[1][0]), mg_two_sum(run[0][1], run[1][1]),
                               mg_two_sum(run[0][2], run[1][2]), mg_two_sum(run[0][3], run[1][3])};
-        cta_col_partials(r2, k, g.c0, tile, part);
+        cta_col_partials(r2, k, g.c0, tile, ta.part);
     }
+    return true;
+}
+
+template <bool UP, bool DOT>
+__global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUtensorMap mr,
+                                                 const __grid_constant__ CUtensorMap mc,
+                                                 const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
+                                                 const float *__restrict__ r, const float *__restrict__ zc,
+                                                 float *__restrict__ out, float2 *part, int *err) {
+    extern __shared__ unsigned char mg_tile_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char *sm = mg_tile_raw + ((128u - (mg_saddr(mg_tile_raw) & 127u)) & 127u);
+    const TileArgs a{F, C, r, zc, out, part, err};
+    mg_tile_body<UP, DOT>(sm, &bar, 0u, true, (int)blockIdx.x, &mr, &mc, &mz, a, k, NoHook{});
 }
 
 // ---- TMA-tiled CG passes on the finest level ---------------------------------------------
@@ -377,9 +411,9 @@ int64_t n_ctiles(const Lvl &F) { return (int64_t)((F.W + CX - 1) / CX) * ((F.H +
 dim3 ctile_grid(const Lvl &F, int k) { return dim3((unsigned)(n_ctiles(F) * ((k + TCB - 1) / TCB))); }
 
 // issue loads (thread 0), then a bounded, CTA-uniform wait
-__device__ __forceinline__ bool ctile_wait(uint64_t *bar, int *err) {
+__device__ __forceinline__ bool ctile_wait(uint64_t *bar, uint32_t parity, int *err) {
     bool done = true;
-    for (uint32_t spins = 0; !mg_try_wait(bar, 0);) {
+    for (uint32_t spins = 0; !mg_try_wait(bar, parity);) {
         if (++spins > kTileSpin) {
             done = false;
             break;
@@ -388,29 +422,32 @@ __device__ __forceinline__ bool ctile_wait(uint64_t *bar, int *err) {
     if (__syncthreads_and(done ? 1 : 0)) return true;
     if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar, 0); ++q) {
+        for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar, parity); ++q) {
         }
     }
     return false;
 }
 
-__device__ __forceinline__ void bar_init_expect(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+// thread 0: (once per CTA, if `init`) initialise the barrier, then expect `bytes` on it
+__device__ __forceinline__ void bar_init_expect(uint64_t *bar, uint32_t bytes, bool init) {
+    if (init) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mg_saddr(bar)), "r"(bytes) : "memory");
 }
 
 struct CGeo {
     int x0, y0, t, c0;
 };
-__device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int &tile) {
+__device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int blk, int &tile) {
     const int ncb = (k + TCB - 1) / TCB;
     const int tx = (F.W + CX - 1) / CX, ty = (F.H + CY - 1) / CY;
     CGeo g;
     const int ntile = tx * ty * F.T;
-    int b = F.cb_outer ? (int)(blockIdx.x % ntile) : (int)(blockIdx.x / ncb);
+    int b = F.cb_outer ? blk % ntile : blk / ncb;
     tile = b;
-    g.c0 = (F.cb_outer ? (int)(blockIdx.x / ntile) : (int)(blockIdx.x % ncb)) * TCB;
+    g.c0 = (F.cb_outer ? blk / ntile : blk % ncb) * TCB;
     g.x0 = (b % tx) * CX;
     b /= tx;
     g.y0 = (b % ty) * CY;
@@ -418,31 +455,31 @@ __device__ __forceinline__ CGeo ctile_geo(const Lvl &F, int k, int &tile) {
     return g;
 }
 
-// p' = z + beta p over the tile; partials of p'.G p' in edge form (pad, east, south, half TSV)
-__global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ CUtensorMap mzt,
-                                                     const __grid_constant__ CUtensorMap mpt,
-                                                     const __grid_constant__ CUtensorMap mct, Lvl F, int k,
-                                                     const float *__restrict__ z, const float *__restrict__ p,
-                                                     const double *__restrict__ beta, float *__restrict__ p_out,
-                                                     float2 *part, int *err) {
-    extern __shared__ unsigned char mg_dir_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    unsigned char *sm = mg_dir_raw + ((128u - (mg_saddr(mg_dir_raw) & 127u)) & 127u);
+// p' = z + beta p over tile block `blk`; partials of p'.G p' in edge form (pad, east, south,
+// half TSV).  False if the wait on the tile's loads expired (error word raised).  The issuing
+// thread runs `hook` while the copies are in flight.
+template <class Hook>
+__device__ __forceinline__ bool mg_dir_body(unsigned char *sm, uint64_t *bar, uint32_t parity, bool init, int blk,
+                                            const CUtensorMap *mzt, const CUtensorMap *mpt, const CUtensorMap *mct,
+                                            const Lvl &F, int k, const float *__restrict__ z,
+                                            const float *__restrict__ p, const double *__restrict__ beta,
+                                            float *__restrict__ p_out, float2 *part, int *err, const Hook &hook) {
     const float *zs = reinterpret_cast<const float *>(sm);
     const float *ps = reinterpret_cast<const float *>(sm + S_V);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + 2 * S_V);
     int tile;
-    const CGeo g = ctile_geo(F, k, tile);
+    const CGeo g = ctile_geo(F, k, blk, tile);
     if (threadIdx.x == 0) {
-        bar_init_expect(&bar, (uint32_t)(2 * S_V + SPY * SPX * 16));
-        mg_tma4(sm, &mzt, &bar, g.c0, g.x0, g.y0, g.t);
-        mg_tma4(sm + S_V, &mpt, &bar, g.c0, g.x0, g.y0, g.t);
-        mg_tma4(sm + 2 * S_V, &mct, &bar, 0, g.x0, g.y0, g.t);
+        bar_init_expect(bar, (uint32_t)(2 * S_V + SPY * SPX * 16), init);
+        mg_tma4(sm, mzt, bar, g.c0, g.x0, g.y0, g.t);
+        mg_tma4(sm + S_V, mpt, bar, g.c0, g.x0, g.y0, g.t);
+        mg_tma4(sm + 2 * S_V, mct, bar, 0, g.x0, g.y0, g.t);
+        hook();
     }
     __shared__ __align__(16) float s_b[TCB];  // beta in FP32, one conversion per column
     if (threadIdx.x < TCB) s_b[threadIdx.x] = g.c0 + (int)threadIdx.x < k ? (float)beta[g.c0 + threadIdx.x] : 0.f;
     __syncthreads();
-    if (!ctile_wait(&bar, err)) return;
+    if (!ctile_wait(bar, parity, err)) return false;
     float run[4] = {0.f, 0.f, 0.f, 0.f};
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
@@ -484,29 +521,40 @@ __global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ 
         f4st(p_out + (int64_t)i * k + col, pv);
     }
     ctile_partials(run, k, g.c0, tile, part);
+    return true;
 }
 
-// r -= alpha G p' with G p' from the staged p' tile; partials of r.D^-1 r; with XPAIR also
-// x += alpha_prev p'_prev + alpha p'
-template <bool XPAIR>
-__global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUtensorMap mpt,
+__global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ CUtensorMap mzt,
+                                                     const __grid_constant__ CUtensorMap mpt,
                                                      const __grid_constant__ CUtensorMap mct, Lvl F, int k,
-                                                     const double *__restrict__ alpha,
-                                                     const double *__restrict__ alpha_prev,
-                                                     const float *__restrict__ p, const float *__restrict__ p_prev,
-                                                     float *__restrict__ x, float *__restrict__ r, float2 *part,
-                                                     int *err) {
-    extern __shared__ unsigned char mg_upd_raw[];
+                                                     const float *__restrict__ z, const float *__restrict__ p,
+                                                     const double *__restrict__ beta, float *__restrict__ p_out,
+                                                     float2 *part, int *err) {
+    extern __shared__ unsigned char mg_dir_raw[];
     __shared__ __align__(8) uint64_t bar;
-    unsigned char *sm = mg_upd_raw + ((128u - (mg_saddr(mg_upd_raw) & 127u)) & 127u);
+    unsigned char *sm = mg_dir_raw + ((128u - (mg_saddr(mg_dir_raw) & 127u)) & 127u);
+    mg_dir_body(sm, &bar, 0u, true, (int)blockIdx.x, &mzt, &mpt, &mct, F, k, z, p, beta, p_out, part, err, NoHook{});
+}
+
+// r -= alpha G p' with G p' from the staged p' tile of block `blk`; partials of r.D^-1 r; with
+// XPAIR also x += alpha_prev p'_prev + alpha p'.  False if the wait on the tile's loads expired.
+// The issuing thread runs `hook` while the copies are in flight.
+template <bool XPAIR, class Hook>
+__device__ __forceinline__ bool mg_upd_body(unsigned char *sm, uint64_t *bar, uint32_t parity, bool init, int blk,
+                                            const CUtensorMap *mpt, const CUtensorMap *mct, const Lvl &F, int k,
+                                            const double *__restrict__ alpha, const double *__restrict__ alpha_prev,
+                                            const float *__restrict__ p, const float *__restrict__ p_prev,
+                                            float *__restrict__ x, float *__restrict__ r, float2 *part, int *err,
+                                            const Hook &hook) {
     const float *ps = reinterpret_cast<const float *>(sm);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + U_V);
     int tile;
-    const CGeo g = ctile_geo(F, k, tile);
+    const CGeo g = ctile_geo(F, k, blk, tile);
     if (threadIdx.x == 0) {
-        bar_init_expect(&bar, (uint32_t)(U_V + UPY * UPX * 16));
-        mg_tma4(sm, &mpt, &bar, g.c0, g.x0 - 1, g.y0 - 1, g.t);
-        mg_tma4(sm + U_V, &mct, &bar, 0, g.x0 - 1, g.y0 - 1, g.t);
+        bar_init_expect(bar, (uint32_t)(U_V + UPY * UPX * 16), init);
+        mg_tma4(sm, mpt, bar, g.c0, g.x0 - 1, g.y0 - 1, g.t);
+        mg_tma4(sm + U_V, mct, bar, 0, g.x0 - 1, g.y0 - 1, g.t);
+        hook();
     }
     // r (and for the x update x and p'_prev) are read straight from global memory after
     // the stencil; ask L2 for their 128-byte row slices now, so that the DRAM reads overlap
@@ -534,7 +582,7 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
         if constexpr (XPAIR) s_ap[threadIdx.x] = j < k ? (float)alpha_prev[j] : 0.f;
     }
     __syncthreads();
-    if (!ctile_wait(&bar, err)) return;
+    if (!ctile_wait(bar, parity, err)) return false;
     float run[4] = {0.f, 0.f, 0.f, 0.f};
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
@@ -581,6 +629,22 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
         run[3] = fmaf(di * rv.w, rv.w, run[3]);
     }
     ctile_partials(run, k, g.c0, tile, part);
+    return true;
+}
+
+template <bool XPAIR>
+__global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUtensorMap mpt,
+                                                     const __grid_constant__ CUtensorMap mct, Lvl F, int k,
+                                                     const double *__restrict__ alpha,
+                                                     const double *__restrict__ alpha_prev,
+                                                     const float *__restrict__ p, const float *__restrict__ p_prev,
+                                                     float *__restrict__ x, float *__restrict__ r, float2 *part,
+                                                     int *err) {
+    extern __shared__ unsigned char mg_upd_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char *sm = mg_upd_raw + ((128u - (mg_saddr(mg_upd_raw) & 127u)) & 127u);
+    mg_upd_body<XPAIR>(sm, &bar, 0u, true, (int)blockIdx.x, &mpt, &mct, F, k, alpha, alpha_prev, p, p_prev, x, r,
+                       part, err, NoHook{});
 }
 
 // coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
@@ -592,11 +656,12 @@ __global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUt
 constexpr int CI_T = 32;
 dim3 cinv_grid(int64_t n, int k) { return dim3((unsigned)((n + CI_T - 1) / CI_T), (unsigned)((k + CI_T - 1) / CI_T)); }
 
-__global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, const float *__restrict__ ainv,
-                                                 const float *__restrict__ r, float *__restrict__ z) {
+// the tile of row block bx and column block by
+__device__ __forceinline__ void mg_cinv_body(int bx, int by, int n, int ld, int k, const float *__restrict__ ainv,
+                                             const float *__restrict__ r, float *__restrict__ z) {
     __shared__ __align__(16) float As[CI_T][CI_T + 4];  // [row][j], rows padded against bank conflicts
     __shared__ __align__(16) float Rs[CI_T][CI_T];      // [j][column]
-    const int row0 = blockIdx.x * CI_T, col0 = blockIdx.y * CI_T;
+    const int row0 = bx * CI_T, col0 = by * CI_T;
     const int ty = threadIdx.x >> 3, tx = (threadIdx.x & 7) * 4;  // this thread: row ty, columns tx .. tx+3
     float4 a0 = zero4(), a1 = zero4();
     for (int j0 = 0; j0 < ld; j0 += CI_T) {
@@ -618,6 +683,11 @@ __global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, const flo
     if (row0 + ty < n && col0 + tx < k) f4st(z + (int64_t)(row0 + ty) * k + col0 + tx, a0 + a1);
 }
 
+__global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, const float *__restrict__ ainv,
+                                                 const float *__restrict__ r, float *__restrict__ z) {
+    mg_cinv_body((int)blockIdx.x, (int)blockIdx.y, n, ld, k, ainv, r, z);
+}
+
 // ---- per-column folds (one CTA per column, partials summed in a fixed tree order) -------
 
 enum { FOLD_ALPHA = 0, FOLD_RR = 1, FOLD_BETA = 2 };
@@ -634,10 +704,10 @@ struct FoldArgs {
     double tol;
 };
 
+// column j of one network's fold
 template <int KIND>
-__global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
+__device__ __forceinline__ void mg_fold_body(const FoldArgs &f, int j) {
     __shared__ float2 s[256];
-    const int j = blockIdx.x;
     float2 acc = make_float2(0.f, 0.f);
     for (int64_t c = threadIdx.x; c < f.chunks; c += blockDim.x) acc = df_plus(acc, f.part[c * f.k + j]);
     s[threadIdx.x] = acc;
@@ -668,19 +738,28 @@ __global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
     }
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(256) k_mg_fold(FoldArgs f) {
+    mg_fold_body<KIND>(f, (int)blockIdx.x);
+}
+
 // after an accurate residual replacement: freeze the columns whose accurate residual meets
 // tol and count the rest.  A column whose recursive residual has run more than 100x below the
 // accurate one, or claims tol while the accurate residual does not, has a stale search direction (the
 // recursion went on past its attainable accuracy): rho = 0 makes the next beta fold
 // restart it (beta = 0), as rescaling a stale direction stalls CG.
-__global__ void k_mg_freeze(int k, const double *resid, const double *relrec, double tol, int *active, double *rho,
-                            int *nact) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
+__device__ __forceinline__ void mg_freeze_col(int j, const double *resid, const double *relrec, double tol,
+                                              int *active, double *rho, int *nact) {
     const double tr = resid[j], rec = relrec[j];
     if (active[j] && (!(rec > 0.0) || rec < 1e-2 * tr || (!(rec > tol) && tr > tol))) rho[j] = 0.0;
     if (active[j] && !(tr > tol)) active[j] = 0;
     if (active[j]) atomicAdd(nact, 1);
+}
+
+__global__ void k_mg_freeze(int k, const double *resid, const double *relrec, double tol, int *active, double *rho,
+                            int *nact) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) mg_freeze_col(j, resid, relrec, tol, active, rho, nact);
 }
 
 unsigned ublocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -1257,117 +1336,660 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     return ER_OK;
 }
 
-// ---- batching form: all networks' multigrid solves in one CUDA graph ------------------------
+// ---- batching form: level-synchronous launches over all networks ---------------------------
 //
-// Each network's sketch, solve and map is one branch of a single graph, so the GPU interleaves
-// the launches of hundreds of uneven networks with no host thread, host poll or
-// synchronisation between them.  A branch runs exactly the kernels of er_sketch + er_solve
-// (multigrid) + er_reff_map on its network; its iteration loop is a device-side WHILE node:
-// the body runs the CG iterations of one poll period, then a one-thread control kernel reads the network's
-// unconverged-column count and error word and either ends the loop (all columns met tol and
-// the accurate residual confirmed it, an error, or maxit) or, through a nested IF node, runs
-// the accurate residual replacement, exactly when the host loop of er_solve would.  Converged
-// networks thus leave the GPU on their own while the others continue.
-
-struct MgBatchState {  // one network of a multigrid batch (device memory)
-    int it, last_replace, replacements, done, err, converged, n_active, pad;
-    double max_resid;
-};
-
-// after the loop body's iterations: count them and decide whether the accurate residual
-// replacement runs (IF node) and, if not, whether the loop continues
-__global__ void k_mgb_after_block(MgBatchState *st, const int *cnt, const int *errw, int block, int replace_every,
-                                  int maxit, cudaGraphConditionalHandle h_repl, cudaGraphConditionalHandle h_loop) {
-    MgBatchState &s = *st;
-    s.it += block;
-    const int e = *errw;
-    if (e) s.err = 1;
-    const bool need = !e && (cnt[0] == 0 || s.it - s.last_replace >= replace_every);
-    cudaGraphSetConditional(h_repl, need ? 1u : 0u);
-    if (!need) cudaGraphSetConditional(h_loop, (!e && s.it < maxit) ? 1u : 0u);
-}
-
-// after an accurate residual replacement (k_mg_freeze counted the columns still above tol)
-__global__ void k_mgb_after_replace(MgBatchState *st, const int *cnt, const int *errw, int maxit,
-                                    cudaGraphConditionalHandle h_loop, int set_loop) {
-    MgBatchState &s = *st;
-    s.last_replace = s.it;
-    s.replacements += 1;
-    s.n_active = cnt[1];
-    s.done = cnt[1] == 0;
-    if (*errw) s.err = 1;
-    if (set_loop) cudaGraphSetConditional(h_loop, (!s.done && !s.err && s.it < maxit) ? 1u : 0u);
-}
-
-// final accurate residuals of the network's k columns: the largest, and whether all meet tol
-__global__ void k_mgb_summary(MgBatchState *st, const double *resid, int k, double tol) {
-    __shared__ double smax[32];
-    __shared__ int sok[32];
-    double mx = 0.0;
-    int ok = 1;
-    for (int j = threadIdx.x; j < k; j += 32) {
-        mx = fmax(mx, resid[j]);
-        ok &= resid[j] <= tol;
-    }
-    smax[threadIdx.x] = mx;
-    sok[threadIdx.x] = ok;
-    __syncwarp();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < 32; ++i) {
-            mx = fmax(mx, smax[i]);
-            ok &= sok[i];
-        }
-        st->max_resid = mx;
-        st->converged = ok;
-    }
-}
+// Hundreds of uneven networks, each with its own hierarchy, vectors and per-column scalars,
+// advance through er_solve's multigrid iteration together: every pass of the iteration (each
+// level's restriction and prolongation, the coarsest solves, the direction and update passes,
+// the folds) is ONE launch over the blocks of all networks still running.  These launches are
+// persistent: a grid of a few CTAs per SM walks a device-side work list, the prefix sums of
+// the running networks' blocks per pass, so a launch costs the same whether 500 networks or
+// one are left.  A CTA maps its item to (network, block) by a binary search of the prefix sums
+// (staged in shared memory) and runs exactly the single-network kernel's body on it: the same
+// tiles, the same arithmetic, the same partial sums, so every network's map is bitwise what
+// er_solve gives it alone.
+//
+// One poll period (er_solve's check_every iterations) is the body of a device-side WHILE node
+// of a CUDA graph.  After the iterations, a control kernel takes each running network's
+// decision exactly where er_solve's host loop would (run the accurate residual replacement,
+// stop on an error or maxit); the replacement passes run over the networks that chose it;
+// then one CTA updates the states, rebuilds the work list of the networks still running
+// (prefix sums per pass) and ends the loop when none is left.  No host thread polls: the host
+// launches the graph once per group of up to kBmgMaxNets networks.
 
 namespace {
 
-struct BatchNet {
-    int c;
-    GridDev *g;
-    Workspace *w;
-    MgHier *h;
-    float *Y, *Z;
-    int cb_outer;
+constexpr int kBmgLv = 12;          // levels per network (2 x 2 aggregation: 4^11 x 512 nodes)
+constexpr int kBmgMaxNets = 1024;   // networks per group: one thread each in the control kernels
+// pass kinds of the work list: 0 .. kBmgLv - 2 the tile pass between levels l and l + 1
+enum { BP_CT = kBmgLv - 1, BP_CINV, BP_N };
+
+struct BmgNet {  // one network of a batch, device resident (the TMA reads the maps from here)
+    CUtensorMap map_r[kBmgLv], map_c[kBmgLv], map_z[kBmgLv];
+    CUtensorMap dmap_z, dmap_p[2], dmap_c, umap_p[2], umap_c;
+    Lvl lv[kBmgLv];          // with the network's launch order in cb_outer
+    float *r[kBmgLv];        // r[0]: the CG residual (the workspace's)
+    float *z[kBmgLv];
+    const float *ainv;       // coarsest level's dense inverse
+    float *p[2], *x;         // search directions, iterate (the caller's Z)
+    float2 *part;
+    double *scal, *msc;
+    int *cnt, *err;
+    FoldArgs fold_beta, fold_ct;
+    int L, ld_inv, nc, cinv_gx;
+    int items[BP_N];         // blocks per pass kind (0: the pass does not reach this network)
 };
 
-// the accurate residual replacement of er_solve's multigrid loop, launched on w.s
-void mgb_replace(const BatchNet &b, double tol) {
-    Workspace &w = *b.w;
-    fp32_accum(*b.g, w, b.Z, nullptr);
-    fp32_residual(*b.g, w, b.Y, tol, 0, 0, nullptr);
-    cudaMemsetAsync(b.h->cnt + 1, 0, sizeof(int), w.s);
-    k_mg_freeze<<<ublocks(w.k, 128), 128, 0, w.s>>>(w.k, w.scal + 4 * w.k, b.h->msc, tol, w.ints, w.scal + 2 * w.k,
-                                                    b.h->cnt + 1);
+struct BmgState {  // one network's loop state (device memory)
+    int it, last_replace, replacements, leave, err, converged;
+    double max_resid;
+};
+
+// list layout (ints): [0] running networks na, [1 .. cap] their indices, then per pass kind
+// the exclusive prefix sums of their blocks, cap + 1 entries each
+__device__ __forceinline__ const int *bmg_pre(const int *list, int cap, int pass) {
+    return list + 1 + cap + pass * (cap + 1);
 }
 
-// add a conditional node to the graph `s` is capturing, after its current dependencies, and
-// make it the capture's only dependency; returns its body graph
-er_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle hnd, cudaGraphConditionalNodeType type,
-                          cudaGraph_t *body) {
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t graph = nullptr;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    ER_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
-    if (cs != cudaStreamCaptureStatusActive) return fail(ER_ERR_CUDA, "stream is not capturing");
-    cudaGraphNodeParams p{};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = hnd;
-    p.conditional.type = type;
-    p.conditional.size = 1;
-    cudaGraphNode_t node;
-    ER_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &p));
-    ER_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    *body = p.conditional.phGraph_out[0];
+// stage a pass's prefix sums in shared memory; returns the number of running networks
+__device__ __forceinline__ int bmg_stage(const int *list, int cap, int pass, int *spre) {
+    const int na = list[0];
+    const int *pre = bmg_pre(list, cap, pass);
+    for (int i = threadIdx.x; i <= na; i += blockDim.x) spre[i] = pre[i];
+    __syncthreads();
+    return na;
+}
+
+// the running network whose blocks hold item i: the largest s with spre[s] <= i
+__device__ __forceinline__ int bmg_slot(const int *spre, int na, int i) {
+    int lo = 0, hi = na - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (spre[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void bmg_bar_init(uint64_t *bar) {
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+// The persistent pass kernels overlap each item's bookkeeping with the previous item's copies:
+// right after issuing item i's bulk copies, the issuing thread finds item i + gridDim.x
+// (network, block, arguments, tensor maps) and writes it to the other of two shared slots, so
+// the next item's copies can start as soon as the CTA's threads are done with the tile.
+
+__device__ __forceinline__ void bmg_prefetch_map(const CUtensorMap *m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+}
+
+struct BmgTileSlot {
+    TileArgs a;
+    const CUtensorMap *mr, *mc, *mz;
+    int blk;
+};
+
+template <bool UP, bool DOT>
+__device__ __forceinline__ void bmg_tile_decode(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                                const int *spre, int na, int l, int i, BmgTileSlot &s) {
+    const int q = bmg_slot(spre, na, i);
+    const BmgNet &N = nets[list[1 + q]];
+    s.blk = i - spre[q];
+    s.a.F = N.lv[l];
+    s.a.C = N.lv[l + 1];
+    s.a.r = N.r[l];
+    s.a.zc = UP ? N.z[l + 1] : nullptr;
+    s.a.out = UP ? N.z[l] : N.r[l + 1];
+    s.a.part = DOT ? N.part : nullptr;
+    s.a.err = N.err;
+    s.mr = &N.map_r[l];
+    s.mc = &N.map_c[l];
+    s.mz = UP ? &N.map_z[l + 1] : nullptr;
+    bmg_prefetch_map(s.mr);
+    bmg_prefetch_map(s.mc);
+    if (UP) bmg_prefetch_map(s.mz);
+}
+
+// the tile pass between levels l and l + 1 of every running network (k_mg_tile's body)
+template <bool UP, bool DOT>
+__global__ void __launch_bounds__(256, 3) k_bmg_tile(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                                  int cap, int l, int k) {
+    extern __shared__ unsigned char bmg_tile_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ BmgTileSlot slot[2];
+    unsigned char *sm = bmg_tile_raw + ((128u - (mg_saddr(bmg_tile_raw) & 127u)) & 127u);
+    int *spre = reinterpret_cast<int *>(sm + T_R + T_C + T_Z);
+    bmg_bar_init(&bar);
+    const int na = bmg_stage(list, cap, l, spre);  // (its __syncthreads also publishes the barrier)
+    const int total = na > 0 ? spre[na] : 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < total)
+        bmg_tile_decode<UP, DOT>(nets, list, spre, na, l, (int)blockIdx.x, slot[0]);
+    __syncthreads();
+    uint32_t parity = 0;
+    int q = 0;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const BmgTileSlot &S = slot[q];
+        const int nx = i + (int)gridDim.x;
+        const auto next = [&]() {
+            if (nx < total) bmg_tile_decode<UP, DOT>(nets, list, spre, na, l, nx, slot[q ^ 1]);
+        };
+        if (!mg_tile_body<UP, DOT>(sm, &bar, parity, false, S.blk, S.mr, S.mc, S.mz, S.a, k, next))
+            return;  // error word raised, this CTA's copies drained
+        parity ^= 1u;
+        q ^= 1;
+        __syncthreads();  // the tile buffers and this item's slot are free
+    }
+}
+
+struct BmgDirSlot {
+    Lvl F;
+    const float *z, *p;
+    const double *beta;
+    float *p_out;
+    float2 *part;
+    int *err;
+    const CUtensorMap *mz, *mp, *mc;
+    int blk;
+};
+
+__device__ __forceinline__ void bmg_dir_decode(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                               const int *spre, int na, int cur, int k, int i, BmgDirSlot &s) {
+    const int q = bmg_slot(spre, na, i);
+    const BmgNet &N = nets[list[1 + q]];
+    s.blk = i - spre[q];
+    s.F = N.lv[0];
+    s.z = N.z[0];
+    s.p = N.p[cur];
+    s.beta = N.scal + k;
+    s.p_out = N.p[1 - cur];
+    s.part = N.part;
+    s.err = N.err;
+    s.mz = &N.dmap_z;
+    s.mp = &N.dmap_p[cur];
+    s.mc = &N.dmap_c;
+    bmg_prefetch_map(s.mz);
+    bmg_prefetch_map(s.mp);
+    bmg_prefetch_map(s.mc);
+}
+
+// p' = z + beta p on the finest level of every running network (k_mg_dir_tile's body)
+__global__ void __launch_bounds__(256, 4) k_bmg_dir(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                                 int cap, int k, int cur) {
+    extern __shared__ unsigned char bmg_dir_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ BmgDirSlot slot[2];
+    unsigned char *sm = bmg_dir_raw + ((128u - (mg_saddr(bmg_dir_raw) & 127u)) & 127u);
+    int *spre = reinterpret_cast<int *>(sm + 2 * S_V + S_C);
+    bmg_bar_init(&bar);
+    const int na = bmg_stage(list, cap, BP_CT, spre);
+    const int total = na > 0 ? spre[na] : 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) bmg_dir_decode(nets, list, spre, na, cur, k, (int)blockIdx.x, slot[0]);
+    __syncthreads();
+    uint32_t parity = 0;
+    int q = 0;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const BmgDirSlot &S = slot[q];
+        const int nx = i + (int)gridDim.x;
+        const auto next = [&]() {
+            if (nx < total) bmg_dir_decode(nets, list, spre, na, cur, k, nx, slot[q ^ 1]);
+        };
+        if (!mg_dir_body(sm, &bar, parity, false, S.blk, S.mz, S.mp, S.mc, S.F, k, S.z, S.p, S.beta, S.p_out, S.part,
+                         S.err, next))
+            return;
+        parity ^= 1u;
+        q ^= 1;
+        __syncthreads();
+    }
+}
+
+struct BmgUpdSlot {
+    Lvl F;
+    const double *alpha, *alpha_prev;
+    const float *p, *p_prev;
+    float *x, *r;
+    float2 *part;
+    int *err;
+    const CUtensorMap *mp, *mc;
+    int blk;
+};
+
+__device__ __forceinline__ void bmg_upd_decode(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                               const int *spre, int na, int cur, int k, int i, BmgUpdSlot &s) {
+    const int q = bmg_slot(spre, na, i);
+    const BmgNet &N = nets[list[1 + q]];
+    s.blk = i - spre[q];
+    s.F = N.lv[0];
+    s.alpha = N.scal;
+    s.alpha_prev = N.msc + k;
+    s.p = N.p[1 - cur];
+    s.p_prev = N.p[cur];
+    s.x = N.x;
+    s.r = N.r[0];
+    s.part = N.part;
+    s.err = N.err;
+    s.mp = &N.umap_p[1 - cur];
+    s.mc = &N.umap_c;
+    bmg_prefetch_map(s.mp);
+    bmg_prefetch_map(s.mc);
+}
+
+// r -= alpha G p' (and with XPAIR the paired x update) of every running network (k_mg_upd_tile's body)
+template <bool XPAIR>
+__global__ void __launch_bounds__(256) k_bmg_upd(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                              int cap, int k, int cur) {
+    extern __shared__ unsigned char bmg_upd_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ BmgUpdSlot slot[2];
+    unsigned char *sm = bmg_upd_raw + ((128u - (mg_saddr(bmg_upd_raw) & 127u)) & 127u);
+    int *spre = reinterpret_cast<int *>(sm + U_V + U_C);
+    bmg_bar_init(&bar);
+    const int na = bmg_stage(list, cap, BP_CT, spre);
+    const int total = na > 0 ? spre[na] : 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) bmg_upd_decode(nets, list, spre, na, cur, k, (int)blockIdx.x, slot[0]);
+    __syncthreads();
+    uint32_t parity = 0;
+    int q = 0;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const BmgUpdSlot &S = slot[q];
+        const int nx = i + (int)gridDim.x;
+        const auto next = [&]() {
+            if (nx < total) bmg_upd_decode(nets, list, spre, na, cur, k, nx, slot[q ^ 1]);
+        };
+        if (!mg_upd_body<XPAIR>(sm, &bar, parity, false, S.blk, S.mp, S.mc, S.F, k, S.alpha, S.alpha_prev, S.p,
+                                S.p_prev, S.x, S.r, S.part, S.err, next))
+            return;
+        parity ^= 1u;
+        q ^= 1;
+        __syncthreads();
+    }
+}
+
+// the coarsest level's exact solve of every running network (k_mg_cinv's body)
+__global__ void __launch_bounds__(256) k_bmg_cinv(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                               int cap, int k) {
+    extern __shared__ int bmg_cinv_pre[];
+    const int na = bmg_stage(list, cap, BP_CINV, bmg_cinv_pre);
+    const int total = na > 0 ? bmg_cinv_pre[na] : 0;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const int s = bmg_slot(bmg_cinv_pre, na, i);
+        const BmgNet &N = nets[list[1 + s]];
+        const int b = i - bmg_cinv_pre[s];
+        mg_cinv_body(b % N.cinv_gx, b / N.cinv_gx, N.nc, N.ld_inv, k, N.ainv, N.r[N.L - 1], N.z[N.L - 1]);
+        __syncthreads();
+    }
+}
+
+// one per-column fold of every running network: item = (network, column)
+template <int KIND>
+__global__ void __launch_bounds__(256) k_bmg_fold(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+                                               int k) {
+    const int na = list[0];
+    for (int i = blockIdx.x; i < na * k; i += gridDim.x) {
+        const BmgNet &N = nets[list[1 + i / k]];
+        mg_fold_body<KIND>(KIND == FOLD_BETA ? N.fold_beta : N.fold_ct, i % k);
+        __syncthreads();
+    }
+}
+
+// after a poll period's iterations, per running network: count them and decide, as er_solve's
+// host loop would, whether the accurate residual replacement runs (need[c]) or, if not,
+// whether the network stops (an error or maxit)
+__global__ void k_bmg_control(const BmgNet *__restrict__ nets, BmgState *st, int *need, int n, int block,
+                              int replace_every, int maxit) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        BmgState &s = st[c];
+        need[c] = 0;
+        if (s.leave) continue;
+        const BmgNet &N = nets[c];
+        s.it += block;
+        const int e = *N.err;
+        if (e) s.err = 1;
+        if (!e && (N.cnt[0] == 0 || s.it - s.last_replace >= replace_every)) {
+            need[c] = 1;
+            N.cnt[1] = 0;  // k_mg_freeze counts the columns still above tol here
+        } else if (e || s.it >= maxit) {
+            s.leave = 1;
+        }
+    }
+}
+
+// the replacement's freeze for every network with need[c] (all networks if need is null)
+__global__ void k_bmg_freeze(const BmgNet *__restrict__ nets, const int *need, int n, int k, double tol) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * k) return;
+    const int c = (int)(t / k), j = (int)(t % k);
+    if (need && !need[c]) return;
+    const BmgNet &N = nets[c];
+    mg_freeze_col(j, N.scal + 4 * k, N.msc, tol, N.fold_ct.active, N.scal + 2 * k, N.cnt + 1);
+}
+
+// exclusive prefix sum over the CTA's threads (blockDim.x a multiple of 32, at most 1024)
+__device__ __forceinline__ int bmg_scan(int v, int *total) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) wsum[lane] = t;  // inclusive sums of the warps
+    }
+    __syncthreads();
+    const int base = w > 0 ? wsum[w - 1] : 0;
+    *total = wsum[nw - 1];
+    __syncthreads();  // wsum is reused by the next scan
+    return base + x - v;
+}
+
+// after the replacement passes: the states of the networks that ran one (as er_solve after its
+// replacement: stop when no column is above tol, on an error or at maxit), then the work list
+// of the networks still running, and the WHILE node's condition.  One CTA of kBmgMaxNets threads.
+__global__ void __launch_bounds__(kBmgMaxNets) k_bmg_compact(const BmgNet *__restrict__ nets, BmgState *st,
+                                                           const int *need, int *list, int n, int cap, int maxit,
+                                                           cudaGraphConditionalHandle h_loop, int set_loop) {
+    const int c = threadIdx.x;
+    int run = 0;
+    if (c < n) {
+        BmgState &s = st[c];
+        const BmgNet &N = nets[c];
+        if (need && need[c]) {
+            s.last_replace = s.it;
+            s.replacements += 1;
+            if (*N.err) s.err = 1;
+            if (N.cnt[1] == 0 || s.err || s.it >= maxit) s.leave = 1;
+        }
+        run = !s.leave;
+    }
+    int na;
+    const int pos = bmg_scan(run, &na);
+    if (run) list[1 + pos] = c;
+    if (c == 0) list[0] = na;
+    for (int p = 0; p < BP_N; ++p) {
+        int tot;
+        const int e = bmg_scan(run ? nets[c].items[p] : 0, &tot);
+        int *pre = list + 1 + cap + p * (cap + 1);
+        if (run) pre[pos] = e;
+        if (c == 0) pre[na] = tot;
+    }
+    if (set_loop && c == 0) cudaGraphSetConditional(h_loop, na > 0 ? 1u : 0u);
+}
+
+// before the loop: error words, states and replacement flags cleared
+__global__ void k_bmg_reset(const BmgNet *__restrict__ nets, BmgState *st, int *need, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    *nets[c].err = 0;
+    st[c] = BmgState{};
+    need[c] = 0;
+}
+
+// the final replacement: its freeze counts from zero
+__global__ void k_bmg_zero_active_count(const BmgNet *__restrict__ nets, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) nets[c].cnt[1] = 0;
+}
+
+// after the final replacement: its bookkeeping, the largest accurate residual of the network's
+// columns and whether all of them meet tol
+__global__ void k_bmg_summary(const BmgNet *__restrict__ nets, BmgState *st, int n, int k, double tol) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const BmgNet &N = nets[c];
+    BmgState &s = st[c];
+    s.replacements += 1;
+    if (*N.err) s.err = 1;
+    double mx = 0.0;
+    int ok = 1;
+    for (int j = 0; j < k; ++j) {
+        const double r = N.scal[4 * k + j];
+        mx = fmax(mx, r);
+        ok &= r <= tol;
+    }
+    s.max_resid = mx;
+    s.converged = ok;
+}
+
+}  // namespace
+
+namespace {
+
+struct BmgBuf {  // a device buffer released on every return path
+    void *p = nullptr;
+    ~BmgBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+template <class K>
+int bmg_grid(K kern, size_t smem, int nsm) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess || occ < 1) occ = 1;
+    return occ * nsm;
+}
+
+size_t bmg_tile_smem(int cap) { return (size_t)T_SMEM + 4 * (size_t)(cap + 1); }
+size_t bmg_dir_smem(int cap) { return (size_t)S_SMEM + 4 * (size_t)(cap + 1); }
+size_t bmg_upd_smem(int cap) { return (size_t)U_SMEM + 4 * (size_t)(cap + 1); }
+
+er_status bmg_attributes() {
+    static std::atomic<bool> done{false};
+    if (done.load()) return ER_OK;
+    const int t = (int)bmg_tile_smem(kBmgMaxNets), d = (int)bmg_dir_smem(kBmgMaxNets),
+              u = (int)bmg_upd_smem(kBmgMaxNets);
+    ER_CUDA(cudaFuncSetAttribute(k_bmg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, t));
+    ER_CUDA(cudaFuncSetAttribute(k_bmg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, t));
+    ER_CUDA(cudaFuncSetAttribute(k_bmg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t));
+    ER_CUDA(cudaFuncSetAttribute(k_bmg_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+    ER_CUDA(cudaFuncSetAttribute(k_bmg_upd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, u));
+    ER_CUDA(cudaFuncSetAttribute(k_bmg_upd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, u));
+    done.store(true);
+    return ER_OK;
+}
+
+// What one group's solve reports back.
+struct BmgOut {
+    std::vector<BmgState> states;
+    int64_t launches = 0;
+};
+
+// One group of at most kBmgMaxNets networks (indices `mem` into grids, each with a hierarchy):
+// head (sketches, r = b, x = 0, the first work list), the graph of the poll-period loop, tail
+// (the final replacement, Z, R, the per-network summary).
+er_status bmg_group(er_grid *const *grids, const std::vector<int> &mem, int k, uint64_t seed,
+                    const int32_t *tile_rows, double *const *R_out, const er_solve_opts &opt, float *const *Y,
+                    float *const *Zs, cudaStream_t us, cudaStream_t cs, int nsm, BmgOut &out) {
+    const int m = (int)mem.size(), cap = m;
+    std::vector<BmgNet> hn((size_t)m);
+    std::vector<BatchItem> items((size_t)m);
+    std::vector<int2> work;
+    int Lmax = 0;
+    for (int i = 0; i < m; ++i) {
+        const int c = mem[(size_t)i];
+        GridDev &g = grids[c]->d;
+        Workspace *w = nullptr;
+        er_status st = get_workspace(&g, k, ER_FP32_REFINE, 0, opt.block_order, &w);
+        if (st == ER_OK) st = fp32_workspace_item(g, *w, Y[i], Zs[i], opt.tol, &items[(size_t)i]);
+        MgHier *h = nullptr;
+        if (st == ER_OK) st = mg_prepare(g, *w, &h);
+        if (st != ER_OK) return st;
+        ER_CUDA(cudaStreamSynchronize(w->s));  // any hierarchy set-up done on the workspace's stream
+        const int L = (int)h->lv.size();
+        if (L < 2 || L > kBmgLv) return fail(ER_ERR_INVALID_ARG, "network outside the batching form's level range");
+        const int cbo = ((tile_rows && tile_rows[c]) ? tile_rows[c] : opt.block_order) == 2 ? 1 : 0;
+        BmgNet &N = hn[(size_t)i];
+        std::memset(&N, 0, sizeof(N));
+        for (int l = 0; l < L; ++l) {
+            N.map_r[l] = h->map_r[(size_t)l];
+            N.map_c[l] = h->map_c[(size_t)l];
+            N.map_z[l] = h->map_z[(size_t)l];
+            N.lv[l] = h->lv[(size_t)l];
+            N.lv[l].cb_outer = cbo;
+            N.r[l] = l == 0 ? static_cast<float *>(w->r[0]) : h->r[(size_t)l];
+            N.z[l] = h->z[(size_t)l];
+        }
+        N.dmap_z = h->dmap_z;
+        N.dmap_c = h->dmap_c;
+        N.umap_c = h->umap_c;
+        for (int b = 0; b < 2; ++b) {
+            N.dmap_p[b] = h->dmap_p[b];
+            N.umap_p[b] = h->umap_p[b];
+            N.p[b] = static_cast<float *>(w->p[b]);
+        }
+        N.ainv = h->ainv;
+        N.ld_inv = h->ld_inv;
+        N.nc = (int)h->lv[(size_t)L - 1].n;
+        const dim3 cg = cinv_grid(N.nc, k);
+        N.cinv_gx = (int)cg.x;
+        N.x = Zs[i];
+        N.part = h->part;
+        N.scal = w->scal;
+        N.msc = h->msc;
+        N.cnt = h->cnt;
+        N.err = w->ints + w->k + w->til.n_colblk;
+        const MgRun run{&g, w, h, k, opt.tol, Zs[i], N.err, cbo};
+        N.fold_beta = fold_args(run, n_tiles(h->lv[1]));
+        N.fold_ct = fold_args(run, n_ctiles(h->lv[0]));
+        N.L = L;
+        for (int l = 0; l + 1 < L; ++l) N.items[l] = (int)tile_grid(h->lv[(size_t)l + 1], k).x;
+        N.items[BP_CT] = (int)ctile_grid(h->lv[0], k).x;
+        N.items[BP_CINV] = (int)(cg.x * cg.y);
+        for (int64_t b = 0; b < w->til.n_ctas(); ++b) work.push_back(make_int2(i, (int)b));
+        Lmax = std::max(Lmax, L);
+    }
+    if ((int64_t)work.size() >= INT32_MAX) return fail(ER_ERR_INVALID_ARG, "batch too large");
+
+    // device copies: networks, batch items, the static (network, block) list of the FP32-form
+    // passes, the running list, replacement flags and states
+    const size_t list_n = 1 + (size_t)cap + (size_t)BP_N * (cap + 1);
+    BmgBuf b_nets, b_items, b_work, b_list, b_need, b_state;
+    ER_CUDA(cudaMalloc(&b_nets.p, (size_t)m * sizeof(BmgNet)));
+    ER_CUDA(cudaMalloc(&b_items.p, (size_t)m * sizeof(BatchItem)));
+    ER_CUDA(cudaMalloc(&b_work.p, std::max<size_t>(work.size(), 1) * sizeof(int2)));
+    ER_CUDA(cudaMalloc(&b_list.p, list_n * sizeof(int)));
+    ER_CUDA(cudaMalloc(&b_need.p, (size_t)m * sizeof(int)));
+    ER_CUDA(cudaMalloc(&b_state.p, (size_t)m * sizeof(BmgState)));
+    ER_CUDA(cudaMemcpyAsync(b_nets.p, hn.data(), (size_t)m * sizeof(BmgNet), cudaMemcpyHostToDevice, us));
+    ER_CUDA(cudaMemcpyAsync(b_items.p, items.data(), (size_t)m * sizeof(BatchItem), cudaMemcpyHostToDevice, us));
+    if (!work.empty())
+        ER_CUDA(cudaMemcpyAsync(b_work.p, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, us));
+    const BmgNet *dn = static_cast<const BmgNet *>(b_nets.p);
+    const BatchItem *di = static_cast<const BatchItem *>(b_items.p);
+    const int2 *dw = static_cast<const int2 *>(b_work.p);
+    const int nw = (int)work.size();
+    int *dl = static_cast<int *>(b_list.p);
+    int *dneed = static_cast<int *>(b_need.p);
+    BmgState *ds = static_cast<BmgState *>(b_state.p);
+    const unsigned nb = (unsigned)((m + 255) / 256);
+    const unsigned nfz = (unsigned)(((int64_t)m * k + 255) / 256);
+
+    // head: network i's sketch uses seed + its index in the call; error words, states; r = b,
+    // x = 0, p = 0, rho0 (er_solve's initialisation); the first work list (every network)
+    for (int i = 0; i < m; ++i) {
+        er_status st = sketch(grids[mem[(size_t)i]], k, seed + (uint64_t)mem[(size_t)i], ER_FP32_REFINE, Y[i], us);
+        if (st != ER_OK) return st;
+    }
+    k_bmg_reset<<<nb, 256, 0, us>>>(dn, ds, dneed, m);
+    er_status st = fp32_batch_pass(MODE_INIT, di, dw, nw, 0, 0, us);
+    if (st != ER_OK) return st;
+    k_bmg_compact<<<1, kBmgMaxNets, 0, us>>>(dn, ds, nullptr, dl, m, cap, opt.maxit, 0, 0);
+    ER_CUDA(cudaGetLastError());
+
+    // the loop: a graph holding one WHILE node whose body is one poll period
+    const int block = std::max(2, opt.check_every + (opt.check_every & 1));
+    const size_t tsm = bmg_tile_smem(cap), dsm = bmg_dir_smem(cap), usm = bmg_upd_smem(cap),
+                 csm = 4 * (size_t)(cap + 1);
+    const int g_down = bmg_grid(k_bmg_tile<false, false>, tsm, nsm), g_up = bmg_grid(k_bmg_tile<true, false>, tsm, nsm),
+              g_up0 = bmg_grid(k_bmg_tile<true, true>, tsm, nsm), g_dir = bmg_grid(k_bmg_dir, dsm, nsm),
+              g_upd1 = bmg_grid(k_bmg_upd<true>, usm, nsm), g_upd0 = bmg_grid(k_bmg_upd<false>, usm, nsm),
+              g_cinv = bmg_grid(k_bmg_cinv, csm, nsm), g_fold = 8 * nsm;
+    struct GraphGuard {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        ~GraphGuard() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+        }
+    } gg;
+    ER_CUDA(cudaGraphCreate(&gg.g, 0));
+    cudaGraphConditionalHandle h_loop;
+    ER_CUDA(cudaGraphConditionalHandleCreate(&h_loop, gg.g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h_loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop_node;
+    ER_CUDA(cudaGraphAddNode(&loop_node, gg.g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ER_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < block; ++it) {
+        const int cur = it & 1;
+        // V-cycle: restriction down the levels, coarsest solves, prolongation up
+        for (int l = 0; l + 1 < Lmax; ++l) k_bmg_tile<false, false><<<g_down, 256, tsm, cs>>>(dn, dl, cap, l, k);
+        k_bmg_cinv<<<g_cinv, 256, csm, cs>>>(dn, dl, cap, k);
+        for (int l = Lmax - 2; l >= 1; --l) k_bmg_tile<true, false><<<g_up, 256, tsm, cs>>>(dn, dl, cap, l, k);
+        k_bmg_tile<true, true><<<g_up0, 256, tsm, cs>>>(dn, dl, cap, 0, k);
+        k_bmg_fold<FOLD_BETA><<<g_fold, 256, 0, cs>>>(dn, dl, k);
+        // CG: direction, step length, update, recursive residual norms
+        k_bmg_dir<<<g_dir, 256, dsm, cs>>>(dn, dl, cap, k, cur);
+        k_bmg_fold<FOLD_ALPHA><<<g_fold, 256, 0, cs>>>(dn, dl, k);
+        if (cur == 1)
+            k_bmg_upd<true><<<g_upd1, 256, usm, cs>>>(dn, dl, cap, k, cur);
+        else
+            k_bmg_upd<false><<<g_upd0, 256, usm, cs>>>(dn, dl, cap, k, cur);
+        k_bmg_fold<FOLD_RR><<<g_fold, 256, 0, cs>>>(dn, dl, k);
+    }
+    k_bmg_control<<<nb, 256, 0, cs>>>(dn, ds, dneed, m, block, opt.replace_every, opt.maxit);
+    fp32_batch_pass(MODE_ACCUM, di, dw, nw, 0, 0, cs, dneed);
+    fp32_batch_pass(MODE_R, di, dw, nw, 0, 0, cs, dneed);
+    k_bmg_freeze<<<nfz, 256, 0, cs>>>(dn, dneed, m, k, opt.tol);
+    k_bmg_compact<<<1, kBmgMaxNets, 0, cs>>>(dn, ds, dneed, dl, m, cap, opt.maxit, h_loop, 1);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture (multigrid batch)");
+    ER_CUDA(cudaGraphInstantiate(&gg.e, gg.g, 0));
+    ER_CUDA(cudaGraphLaunch(gg.e, us));
+
+    // tail: the final replacement (a no-op on the iterate when the loop ended on one), Z, R
+    k_bmg_zero_active_count<<<nb, 256, 0, us>>>(dn, m);
+    st = fp32_batch_pass(MODE_ACCUM, di, dw, nw, 0, 0, us);
+    if (st == ER_OK) st = fp32_batch_pass(MODE_R, di, dw, nw, 0, 0, us);
+    if (st != ER_OK) return st;
+    k_bmg_freeze<<<nfz, 256, 0, us>>>(dn, nullptr, m, k, opt.tol);
+    st = fp32_batch_pass(MODE_UNSCALE, di, dw, nw, 0, 0, us);
+    for (int i = 0; i < m && st == ER_OK; ++i)
+        st = reff_map(grids[mem[(size_t)i]], Zs[i], k, ER_FP32_REFINE, R_out[mem[(size_t)i]], us);
+    if (st != ER_OK) return st;
+    k_bmg_summary<<<nb, 256, 0, us>>>(dn, ds, m, k, opt.tol);
+    ER_CUDA(cudaGetLastError());
+    out.states.resize((size_t)m);
+    ER_CUDA(cudaMemcpyAsync(out.states.data(), ds, (size_t)m * sizeof(BmgState), cudaMemcpyDeviceToHost, us));
+    ER_CUDA(cudaStreamSynchronize(us));
+    int max_it = 0;
+    for (const BmgState &s : out.states) max_it = std::max(max_it, s.it);
+    // head: sketches, reset, init, list; per period: the iterations' passes, control, two
+    // replacement passes, freeze, list; tail: 5 passes, the maps, the summary
+    out.launches = (int64_t)m + 3 + (int64_t)(max_it / block) * (block * (2 * Lmax + 4) + 5) + 5 + m + 1;
     return ER_OK;
 }
 
 }  // namespace
 
-er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, const int32_t *tile_rows,
+er_status mg_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t seed, const int32_t *tile_rows,
                          double *const *R_out, const er_solve_opts &opt, er_batch_stats *stats, cudaStream_t us,
                          std::chrono::steady_clock::time_point t0) {
     // every grid is used by this call alone (address order, so concurrent callers cannot deadlock)
@@ -1376,165 +1998,90 @@ er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
     std::vector<std::unique_lock<std::mutex>> locks;
     locks.reserve((size_t)n);
     for (er_grid *g : by_addr) locks.emplace_back(g->mu);
-    // largest networks first: their branches start first
+    // largest networks first: their blocks lead every pass's work list
     std::vector<int> order((size_t)n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return grids[a]->d.n > grids[b]->d.n; });
-
-    struct Bufs {
-        void *yz = nullptr, *state = nullptr;
-        cudaStream_t s[3] = {nullptr, nullptr, nullptr};
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        ~Bufs() {
-            if (exec) cudaGraphExecDestroy(exec);
-            if (graph) cudaGraphDestroy(graph);
-            for (cudaStream_t x : s)
-                if (x) cudaStreamDestroy(x);
-            if (state) cudaFree(state);
-            if (yz) cudaFree(yz);
-        }
-    } B;
+    // every network's sketch Y and solution Z
     std::vector<size_t> off((size_t)n);
     size_t tot = 0;
     for (int c = 0; c < n; ++c) {
-        off[c] = tot;
+        off[(size_t)c] = tot;
         tot += ((size_t)grids[c]->d.n * k * sizeof(float) + 255) & ~(size_t)255;
     }
-    ER_CUDA(cudaMalloc(&B.yz, 2 * tot));
-    ER_CUDA(cudaMalloc(&B.state, (size_t)n * sizeof(MgBatchState)));
-    for (cudaStream_t &x : B.s) ER_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
-    MgBatchState *dstate = static_cast<MgBatchState *>(B.state);
+    BmgBuf yz;
+    ER_CUDA(cudaMalloc(&yz.p, 2 * tot));
+    auto Yof = [&](int c) { return reinterpret_cast<float *>(static_cast<char *>(yz.p) + off[(size_t)c]); };
+    auto Zof = [&](int c) { return reinterpret_cast<float *>(static_cast<char *>(yz.p) + tot + off[(size_t)c]); };
 
-    std::vector<BatchNet> nets;
-    nets.reserve((size_t)n);
-    int32_t iters = 0, reps = 0, conv = 0, launches = 0;
-    int64_t nodes = 0;
+    int32_t iters = 0, reps = 0, conv = 0;
+    int64_t launches = 0, nodes = 0;
     double mx = 0.0;
     bool err = false, unconv = false;
+    std::vector<int> big;
     for (int q = 0; q < n; ++q) {
         const int c = order[(size_t)q];
         GridDev &g = grids[c]->d;
-        if (g.n <= 512 || std::max(g.W, g.H) <= 1) {
-            // a network that is its own coarsest level: er_solve runs it with Jacobi; it is
-            // solved here, before the graph, with exactly er_solve's kernels
-            float *Y = reinterpret_cast<float *>(static_cast<char *>(B.yz) + off[c]);
-            float *Z = reinterpret_cast<float *>(static_cast<char *>(B.yz) + tot + off[c]);
-            er_solve_stats ss{};
-            er_status st = sketch(grids[c], k, seed + (uint64_t)c, ER_FP32_REFINE, Y, us);
-            if (st == ER_OK) st = solve_locked(grids[c], Y, Z, k, ER_FP32_REFINE, &opt, &ss, us);
-            const bool nc = st == ER_ERR_NOT_CONVERGED;
-            if (st != ER_OK && !nc) return st;
-            st = reff_map(grids[c], Z, k, ER_FP32_REFINE, R_out[c], us);
-            if (st != ER_OK) return st;
-            unconv |= nc;
-            iters = std::max(iters, ss.iterations);
-            reps = std::max(reps, ss.sweeps);
-            conv += ss.converged_cols == k;
-            nodes += g.n - g.n_floating;
-            mx = std::max(mx, ss.max_rel_residual);
-            for (int i = 0; i < ER_N_PASS; ++i) launches += ss.launches[i];
-            launches += 2;
+        if (g.n > 512 && std::max(g.W, g.H) > 1) {
+            big.push_back(c);
             continue;
         }
-        BatchNet b{};
-        b.c = c;
-        b.g = &g;
-        b.Y = reinterpret_cast<float *>(static_cast<char *>(B.yz) + off[c]);
-        b.Z = reinterpret_cast<float *>(static_cast<char *>(B.yz) + tot + off[c]);
-        // per network launch order (the autotuner's choice): 2 column blocks outermost
-        b.cb_outer = ((tile_rows && tile_rows[c]) ? tile_rows[c] : opt.block_order) == 2 ? 1 : 0;
-        er_status st = get_workspace(&g, k, ER_FP32_REFINE, 0, opt.block_order, &b.w);
+        // a network that is its own coarsest level: er_solve runs it with Jacobi; so does this
+        er_solve_stats ss{};
+        er_status st = sketch(grids[c], k, seed + (uint64_t)c, ER_FP32_REFINE, Yof(c), us);
+        if (st == ER_OK) st = solve_locked(grids[c], Yof(c), Zof(c), k, ER_FP32_REFINE, &opt, &ss, us);
+        const bool nc = st == ER_ERR_NOT_CONVERGED;
+        if (st != ER_OK && !nc) return st;
+        st = reff_map(grids[c], Zof(c), k, ER_FP32_REFINE, R_out[c], us);
         if (st != ER_OK) return st;
-        st = fp32_prepare(g, *b.w, b.Y, b.Z);
-        if (st != ER_OK) return st;
-        st = mg_prepare(g, *b.w, &b.h);
-        if (st != ER_OK) return st;
-        nets.push_back(b);
+        unconv |= nc;
+        iters = std::max(iters, ss.iterations);
+        reps = std::max(reps, ss.sweeps);
+        conv += ss.converged_cols == k;
+        nodes += g.n - g.n_floating;
+        mx = std::max(mx, ss.max_rel_residual);
+        for (int i = 0; i < ER_N_PASS; ++i) launches += ss.launches[i];
+        launches += 2;
     }
-
-    // iterations per loop body: er_solve's poll period, so that every decision falls where the
-    // host loop makes it
-    const int block = std::max(2, opt.check_every + (opt.check_every & 1));
-    ER_CUDA(cudaGraphCreate(&B.graph, 0));
-    if (nets.empty()) {  // every network was small
-        ER_CUDA(cudaStreamSynchronize(us));
-    }
-    cudaStream_t cs = B.s[0], cs2 = B.s[1], cs3 = B.s[2];
-    // every network is an independent branch (limiting them to 8-64 chains of networks run one
-    // after another measured the same throughput)
-    for (BatchNet &b : nets) {
-        Workspace &w = *b.w;
-        cudaStream_t saved = w.s;
-        MgRun m{b.g, &w, b.h, k, opt.tol, b.Z, w.ints + w.k + w.til.n_colblk, b.cb_outer};
-        MgBatchState *sp = dstate + b.c;
-        cudaGraphConditionalHandle h_loop;
-        ER_CUDA(cudaGraphConditionalHandleCreate(&h_loop, B.graph, 1, cudaGraphCondAssignDefault));
-        er_status st = ER_OK;
-        // head: sketch, cleared error word and state, r = b, x = 0, p = 0
-        ER_CUDA(cudaStreamBeginCaptureToGraph(cs, B.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        w.s = cs;
-        st = sketch(grids[b.c], k, seed + (uint64_t)b.c, ER_FP32_REFINE, b.Y, cs);
-        cudaMemsetAsync(m.err, 0, sizeof(int), cs);
-        cudaMemsetAsync(sp, 0, sizeof(MgBatchState), cs);
-        fp32_init(*b.g, w, b.Y, b.Z, opt.tol, nullptr);
-        cudaGraph_t body = nullptr;
-        if (st == ER_OK) st = add_conditional(cs, h_loop, cudaGraphCondTypeWhile, &body);
-        if (st == ER_OK) {
-            // loop body: `block` iterations, the control kernel, and the replacement under an IF node
-            cudaGraphConditionalHandle h_repl;
-            ER_CUDA(cudaGraphConditionalHandleCreate(&h_repl, body, 0, cudaGraphCondAssignDefault));
-            ER_CUDA(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            w.s = cs2;
-            int cur = 0;
-            for (int i = 0; i < block; ++i) cur = mg_iterate(m, cur, nullptr);
-            k_mgb_after_block<<<1, 1, 0, cs2>>>(sp, b.h->cnt, m.err, block, opt.replace_every, opt.maxit, h_repl, h_loop);
-            cudaGraph_t rbody = nullptr;
-            st = add_conditional(cs2, h_repl, cudaGraphCondTypeIf, &rbody);
-            if (st == ER_OK) {
-                ER_CUDA(cudaStreamBeginCaptureToGraph(cs3, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-                w.s = cs3;
-                mgb_replace(b, opt.tol);
-                k_mgb_after_replace<<<1, 1, 0, cs3>>>(sp, b.h->cnt, m.err, opt.maxit, h_loop, 1);
-                cudaGraph_t tmp;
-                ER_CUDA(cudaStreamEndCapture(cs3, &tmp));
+    int graphs = 0;
+    if (!big.empty()) {
+        er_status st = bmg_attributes();
+        if (st != ER_OK) return st;
+        int nsm = 0;
+        ER_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, grids[big[0]]->d.device));
+        cudaStream_t cs = nullptr;
+        ER_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        struct StreamGuard {
+            cudaStream_t s;
+            ~StreamGuard() { cudaStreamDestroy(s); }
+        } sg{cs};
+        for (size_t g0 = 0; g0 < big.size(); g0 += kBmgMaxNets) {
+            const std::vector<int> mem(big.begin() + (ptrdiff_t)g0,
+                                       big.begin() + (ptrdiff_t)std::min(big.size(), g0 + kBmgMaxNets));
+            std::vector<float *> Y, Z;
+            for (int c : mem) {
+                Y.push_back(Yof(c));
+                Z.push_back(Zof(c));
             }
-            cudaGraph_t tmp;
-            ER_CUDA(cudaStreamEndCapture(cs2, &tmp));
+            BmgOut out;
+            st = bmg_group(grids, mem, k, seed, tile_rows, R_out, opt, Y.data(), Z.data(), us, cs, nsm, out);
+            if (st != ER_OK) return st;
+            ++graphs;
+            launches += out.launches;
+            for (size_t i = 0; i < mem.size(); ++i) {
+                const BmgState &x = out.states[i];
+                const GridDev &g = grids[mem[i]]->d;
+                iters = std::max(iters, x.it);
+                reps = std::max(reps, x.replacements);
+                conv += x.converged;
+                err |= x.err != 0;
+                unconv |= !x.converged;
+                nodes += g.n - g.n_floating;
+                mx = std::max(mx, x.max_resid);
+            }
         }
-        // tail: the final replacement (a no-op on the iterate when the loop ended on one), Z, R
-        w.s = cs;
-        mgb_replace(b, opt.tol);
-        k_mgb_after_replace<<<1, 1, 0, cs>>>(sp, b.h->cnt, m.err, opt.maxit, h_loop, 0);
-        fp32_final(*b.g, w, b.Z, nullptr);
-        if (st == ER_OK) st = reff_map(grids[b.c], b.Z, k, ER_FP32_REFINE, R_out[b.c], cs);
-        k_mgb_summary<<<1, 32, 0, cs>>>(sp, w.scal + 4 * w.k, w.k, opt.tol);
-        cudaGraph_t tmp;
-        const cudaError_t ce = cudaStreamEndCapture(cs, &tmp);
-        w.s = saved;
-        if (st != ER_OK) return st;
-        if (ce != cudaSuccess) return cuda_fail(ce, "graph capture (multigrid batch)");
-    }
-    if (!nets.empty()) {
-        ER_CUDA(cudaGraphInstantiate(&B.exec, B.graph, 0));
-        ER_CUDA(cudaGraphLaunch(B.exec, us));
-    }
-    std::vector<MgBatchState> hs((size_t)n);
-    ER_CUDA(cudaMemcpyAsync(hs.data(), dstate, hs.size() * sizeof(MgBatchState), cudaMemcpyDeviceToHost, us));
-    ER_CUDA(cudaStreamSynchronize(us));
-    for (const BatchNet &b : nets) {
-        const MgBatchState &x = hs[(size_t)b.c];
-        const int L = (int)b.h->lv.size();
-        iters = std::max(iters, x.it);
-        reps = std::max(reps, x.replacements);
-        conv += x.converged;
-        err |= x.err != 0;
-        unconv |= !x.converged;
-        nodes += b.g->n - b.g->n_floating;
-        mx = std::max(mx, x.max_resid);
-        // per iteration: the V-cycle (2L - 1), its fold, direction, update and two folds, plus the
-        // control kernel per two iterations; per replacement 4; head 3; tail 7
-        launches += x.it * (2 * L + 4) + x.it / block + 4 * x.replacements + 3 + 7;
+    } else {
+        ER_CUDA(cudaStreamSynchronize(us));
     }
     if (stats) {
         stats->n_grids = n;
@@ -1544,8 +2091,8 @@ er_status mg_batch_graph(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
         stats->nodes = nodes;
         stats->max_rel_residual = mx;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        stats->launches = launches;
-        stats->graph_captures = nets.empty() ? 0 : 1;
+        stats->launches = (int32_t)std::min<int64_t>(launches, INT32_MAX);
+        stats->graph_captures = graphs;
     }
     if (err) return fail(ER_ERR_TIMEOUT, "a bounded wait on a bulk copy expired inside a solver kernel");
     if (unconv) return fail(ER_ERR_NOT_CONVERGED, "maxit reached with networks still above tol");

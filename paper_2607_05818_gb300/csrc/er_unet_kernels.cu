@@ -748,8 +748,15 @@ struct WgTcArgs {
     int cin, c1, c2, cout, bn, tiles_c1, tiles_c, blocks_per_split, n_blocks;
     int nb, h, wd, bx, by, bimg;
     int stages;
+    int vec4;  // dW rows start on 16-byte boundaries: the epilogue adds 4 columns per reduction
     int *err;
 };
+
+// dst[0..3] += v[0..3] as one 16-byte reduction in L2 (dst 16-byte aligned)
+__device__ __forceinline__ void red_add_v4(float *dst, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
 
 // MN-major operand descriptor, 128-byte swizzle: channel atoms (64 x 8) `lbo` bytes apart,
 // groups of 8 pixels 1,024 bytes apart, descriptor version 1, swizzle mode 2 (128B)
@@ -872,9 +879,15 @@ __global__ void __launch_bounds__(192, 1)
                 tc_ld16(tbase + (uint32_t)cc, v);
                 if (o < a.cout) {
                     float *dst = a.dw + ((int64_t)o * 9 + kk) * a.cin + cbase + cc;
+                    if (a.vec4) {  // csrc % 32 == 0: a group of 4 columns is all in or all out
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (cx + cc + j < csrc) atomicAdd(dst + j, v[j]);
+                        for (int j = 0; j < 16; j += 4)
+                            if (cx + cc + j < csrc) red_add_v4(dst + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (cx + cc + j < csrc) atomicAdd(dst + j, v[j]);
+                    }
                 }
             }
         }
@@ -1526,6 +1539,7 @@ static cudaError_t unet_wgrad3x3_tc(const UConv &c, const __nv_bfloat16 *dy, flo
     a.tiles_c = a.tiles_c1 + (c.c2 + bn - 1) / bn;
     a.nb = c.nb; a.h = c.h; a.wd = c.w_; a.bx = bx; a.by = by; a.bimg = bimg;
     a.stages = stages;
+    a.vec4 = (reinterpret_cast<uintptr_t>(dw) % 16 == 0) ? 1 : 0;  // cin % 32 == 0 keeps every row aligned
     a.err = err_word();
     if (!a.err) return cudaErrorInvalidSymbol;
     const int64_t M = (int64_t)c.nb * c.h * c.w_;

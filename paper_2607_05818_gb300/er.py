@@ -357,9 +357,9 @@ def stack_pairs(M, N, r, s, tsv_xy, Rt, bumps, loads, R, stream=None):
 def batch_solve(grids, k: int, seed: int, R_out, prec="fp32", opts: er_solve_opts | None = None,
                 tile_rows=None, stream=None, allow_unconverged=False):
     """Batching form: R maps of many networks; network c uses seed + c.  With opts.precond 0
-    (Jacobi) every pass is one shared launch over all networks; with precond 1 every network's
-    multigrid solve is one branch of a single CUDA graph, its iteration loop a device-side
-    conditional node.  R_out: list of device FP64 tensors (one per grid)."""
+    (Jacobi) every pass is one shared launch over all networks; with precond 1 every pass of the
+    multigrid iteration is one persistent launch over all running networks and the loop is a
+    device-side conditional graph node.  R_out: list of device FP64 tensors (one per grid)."""
     n = len(grids)
     hs = (c_void_p * n)(*[g.handle.value if isinstance(g.handle, c_void_p) else g.handle for g in grids])
     rs = (c_void_p * n)(*[_ptr(r) for r in R_out])

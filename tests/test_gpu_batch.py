@@ -79,11 +79,11 @@ def test_batch_rejects_fp64_and_bad_args(er):
 
 
 def test_multigrid_batch_equals_single_solves(er):
-    """precond = 1: every network's sketch + multigrid solve + map is one branch of a single
-    CUDA graph, its iteration loop a device-side conditional node, with exactly er_solve's
-    kernels and decisions; so each map is bitwise the map of sketch + solve + map on that
-    network alone, and within the FP32 form's bound of the oracle.  Networks too small for a
-    hierarchy (the 5 x 3 and 20 x 19 ones) take er_solve's Jacobi path, as alone."""
+    """precond = 1: every pass of the multigrid iteration is one persistent launch over all
+    running networks, each block running er_solve's kernel body, and the loop's decisions are
+    er_solve's; so each map is bitwise the map of sketch + solve + map on that network alone,
+    and within the FP32 form's bound of the oracle.  Networks too small for a hierarchy (the
+    5 x 3 and 20 x 19 ones) take er_solve's Jacobi path, as alone."""
     nets = make_batch()
     k, seed = 32, 515
     grids = [er.grid_create(n) for n in nets]
