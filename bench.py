@@ -1043,9 +1043,9 @@ def run_ours(args, rank, world, local_rank):
     rl = []
     n_levels = None
     if mg:
-        n_levels = 1
+        n_levels = 1  # the library coarsens 2 x 2 per tier until a level has at most 1,024 nodes
         Wl, Hl = inst.W, inst.H
-        while max(Wl, Hl) > 8:
+        while inst.T * Wl * Hl > 1024 and max(Wl, Hl) > 1:
             Wl, Hl, n_levels = (Wl + 1) // 2, (Hl + 1) // 2, n_levels + 1
     for idx, name, nbytes in kinds:
         n_l = int(launches[idx])

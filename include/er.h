@@ -200,8 +200,8 @@ er_status er_sketch_cols(er_grid *g, int32_t k_total, int32_t j0, int32_t k_loca
  * Galerkin product P^T G P of a network's matrix is again a network (segments between
  * aggregates kept, those inside dropped, parallel TSVs and pads of an aggregate merged into
  * one), every level is a grid built like er_grid_create's.  Coarsening stops at the first
- * level of at most 512 nodes, which is solved exactly by its dense inverse (FP64 Cholesky on
- * the host, stored in FP32); one damped-Jacobi sweep (weight 0.8) runs before and after each
+ * level of at most 1,024 nodes, which is solved exactly by its dense inverse (FP64 Cholesky on
+ * the host cores, stored in FP32); one damped-Jacobi sweep (weight 0.8) runs before and after each
  * coarse correction, so the cycle is a fixed symmetric positive definite operator, as CG
  * needs.  The hierarchy is built on the first such call and cached on the grid.  A grid that
  * does not coarsen to at most 2,048 nodes (too many tiers) returns ER_ERR_INVALID_ARG.  The library allocates (and caches on the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at
@@ -261,7 +261,7 @@ typedef struct {
  *     and rebuilds the work list, so converged networks leave while the others continue and
  *     no host thread polls.  Every block runs the single-network kernel's body, so each map
  *     equals the single-network map (er_sketch + er_solve + er_reff_map) bitwise.  Networks
- *     of at most 512 nodes (their own coarsest level) are solved first
+ *     of at most 1,024 nodes (their own coarsest level) are solved first
  *     with er_solve's Jacobi path, as alone.  A grid may appear only once
  *     (ER_ERR_INVALID_ARG otherwise).  tile_rows[c] (nullable) is network c's launch order
  *     as er_solve_opts.block_order (the autotuner's choice per size class; 0 = opts'); it

@@ -11,6 +11,10 @@
 
 namespace er {
 
+// The FP32 form's multigrid coarsens until a level has at most this many nodes and solves that
+// level exactly by its dense inverse; a grid this small is solved without the multigrid.
+constexpr int kMgCoarseNodes = 1024;
+
 // Thread-local error message behind er_last_error().
 void set_error(const std::string &msg);
 er_status fail(er_status s, const std::string &msg);

@@ -18,7 +18,7 @@
 //   * the pre-sweep and restriction are one kernel per level, and prolongation and post-sweep
 //     another: a CTA owns 16 x 4 aggregates (32 x 8 nodes of the finer level) and 32 RHS
 //     columns, staged with a one-node halo by cp.async.bulk.tensor; z0 is never stored, it is
-//     recomputed from r; the coarsest level (at most 512 nodes) is solved exactly by its dense
+//     recomputed from r; the coarsest level (at most 1,024 nodes) is solved exactly by its dense
 //     inverse.
 // The CG recursion is the FP32 form's (FP32 vectors, double-float dot sums, double-float
 // iterate with the accurate residual substituted every replace_every iterations, and whenever
@@ -37,6 +37,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -49,7 +50,7 @@ namespace {
 
 constexpr float kOmega = 0.8f;    // damped-Jacobi weight of the smoother
 constexpr float kScale = 1.6f;    // over-correction of the coarse-grid correction
-constexpr int kCoarseTarget = 512;   // coarsen until a level has at most this many nodes
+constexpr int kCoarseTarget = kMgCoarseNodes;  // coarsen until a level has at most this many nodes
 constexpr int kCoarseMax = 2048;     // largest coarsest level (solved by its dense inverse)
 constexpr int kMaxSteps = 16;        // node steps per CTA in the streaming layout
 constexpr int kMinCtas = 1216;       // small levels: fewer steps, so at least 8 CTAs per SM
@@ -87,12 +88,32 @@ Lay make_lay(int64_t n, int k) {
 
 __device__ __forceinline__ float4 f4ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void f4st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ float4 operator+(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float4 operator-(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-__device__ __forceinline__ float4 operator*(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
-__device__ __forceinline__ float4 operator*(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
-__device__ __forceinline__ float4 fma4(float s, float4 a, float4 c) {
-    return make_float4(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y), fmaf(s, a.z, c.z), fmaf(s, a.w, c.w));
+// Four-column arithmetic on the packed FP32 pipe: every float4 operation is two f32x2
+// instructions (each lane rounded exactly as the scalar operation), so the stencil bodies
+// issue half the FP32 instructions.  a - b is formed as fma(b, -1, a), which rounds once.
+__device__ __forceinline__ float2 f2lo(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 f2hi(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 f4of(float2 l, float2 h) { return make_float4(l.x, l.y, h.x, h.y); }
+__device__ __forceinline__ float4 operator+(float4 a, float4 b) {
+    return f4of(__fadd2_rn(f2lo(a), f2lo(b)), __fadd2_rn(f2hi(a), f2hi(b)));
+}
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) {
+    const float2 m = make_float2(-1.f, -1.f);
+    return f4of(__ffma2_rn(f2lo(b), m, f2lo(a)), __ffma2_rn(f2hi(b), m, f2hi(a)));
+}
+__device__ __forceinline__ float4 operator*(float s, float4 a) {
+    const float2 s2 = make_float2(s, s);
+    return f4of(__fmul2_rn(s2, f2lo(a)), __fmul2_rn(s2, f2hi(a)));
+}
+__device__ __forceinline__ float4 operator*(float4 a, float4 b) {
+    return f4of(__fmul2_rn(f2lo(a), f2lo(b)), __fmul2_rn(f2hi(a), f2hi(b)));
+}
+__device__ __forceinline__ float4 fma4(float s, float4 a, float4 c) {  // s * a + c
+    const float2 s2 = make_float2(s, s);
+    return f4of(__ffma2_rn(s2, f2lo(a), f2lo(c)), __ffma2_rn(s2, f2hi(a), f2hi(c)));
+}
+__device__ __forceinline__ float4 fma4v(float4 a, float4 b, float4 c) {  // a * b + c per column
+    return f4of(__ffma2_rn(f2lo(a), f2lo(b), f2lo(c)), __ffma2_rn(f2hi(a), f2hi(b), f2hi(c)));
 }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
@@ -245,9 +266,9 @@ __device__ __forceinline__ void cta_col_partials(const float2 (&run)[4], int k, 
         if (col < k) part[(int64_t)tile * k + col] = acc;
     }
 }
-__device__ __forceinline__ void ctile_partials(const float (&run)[4], int k, int c0, int tile, float2 *part) {
-    const float2 r2[4] = {make_float2(run[0], 0.f), make_float2(run[1], 0.f), make_float2(run[2], 0.f),
-                          make_float2(run[3], 0.f)};
+__device__ __forceinline__ void ctile_partials(float4 run, int k, int c0, int tile, float2 *part) {
+    const float2 r2[4] = {make_float2(run.x, 0.f), make_float2(run.y, 0.f), make_float2(run.z, 0.f),
+                          make_float2(run.w, 0.f)};
     cta_col_partials(r2, k, c0, tile, part);
 }
 
@@ -266,6 +287,69 @@ struct NoHook {
     __device__ void operator()() const {}
 };
 
+// One item of the tile pass between levels F (finer) and C: aggregate (X, Y) of tier t and the
+// 4 columns from `col`.  The accessors give, at tile-local finer-level node (ly, lx) (the
+// one-node halo included: ly 0 .. TFY-1, lx 0 .. TFX-1), the coefficients csm(ly, lx), the
+// residual rsm(ly, lx) and the smoothed field sval(ly, lx) (w D^-1 r, for UP plus the scaled
+// coarse correction); vtsv(j, i) is the smoothed field at node j, the TSV partner of node i
+// on another tier.  UP: z = v + w D^-1 (r - G v) at the aggregate's four nodes is written to
+// `out` and r.z added to `run`; !UP: returns the restricted residual P^T (r - G v) of the
+// aggregate.  Every path that forms these values calls this function, so they agree bitwise.
+template <bool UP, bool DOT, class CS, class RS, class SV, class VT>
+__device__ __forceinline__ float4 mg_agg(const Lvl &F, int k, int t, int X, int Y, int ax, int ay, int col,
+                                         const CS &csm, const RS &rsm, const SV &sval, const VT &vtsv, float *out,
+                                         float4 &run) {
+    float4 acc = zero4();
+    // the smoothed field at the aggregate's own four nodes, computed once: each is the
+    // centre of one stencil and a neighbour in two others (only the ring outside the
+    // aggregate is evaluated per use, once each)
+    const int lx0 = 1 + 2 * ax, ly0 = 1 + 2 * ay;
+    float4 sv[2][2];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) sv[dy][dx] = sval(ly0 + dy, lx0 + dx);
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const int x = 2 * X + dx, y = 2 * Y + dy;
+            if (x >= F.W || y >= F.H) continue;
+            const int lx = lx0 + dx, ly = ly0 + dy;
+            const float4 c = csm(ly, lx);
+            const int i = (t * F.H + y) * F.W + x;
+            if (c.x == 0.f) {  // floating node: not in P, z = 0
+                if constexpr (UP) f4st(out + (int64_t)i * k + col, zero4());
+                continue;
+            }
+            const float4 ri = rsm(ly, lx);
+            const float4 vi = sv[dy][dx];
+            float4 gv = c.w * vi;
+            if (c.y != 0.f) gv = fma4(c.y, vi - (dx == 0 ? sv[dy][1] : sval(ly, lx + 1)), gv);
+            {
+                const float gw = csm(ly, lx - 1).y;
+                if (gw != 0.f) gv = fma4(gw, vi - (dx == 1 ? sv[dy][0] : sval(ly, lx - 1)), gv);
+            }
+            if (c.z != 0.f) gv = fma4(c.z, vi - (dy == 0 ? sv[1][dx] : sval(ly + 1, lx)), gv);
+            {
+                const float gn = csm(ly - 1, lx).z;
+                if (gn != 0.f) gv = fma4(gn, vi - (dy == 1 ? sv[0][dx] : sval(ly - 1, lx)), gv);
+            }
+            if (c.x < 0.f) {
+                const int32_t e1 = F.tsv_ptr[i + 1];
+                for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) gv = fma4(F.tsv_g[e], vi - vtsv(F.tsv_nbr[e], i), gv);
+            }
+            if constexpr (UP) {
+                const float4 zo = fma4(kOmega * fabsf(c.x), ri - gv, vi);
+                f4st(out + (int64_t)i * k + col, zo);
+                if constexpr (DOT) run = fma4v(ri, zo, run);
+            } else {
+                acc = acc + (ri - gv);
+            }
+        }
+    return acc;
+}
+
 // prolongation + post-sweep (UP) or pre-sweep + restriction (!UP) over tile block `blk` of the
 // level pair (ta.F, ta.C); false if the wait on the tile's loads expired (error word raised).
 // `ta` may live in shared memory (read where used) or be built from kernel parameters.
@@ -282,7 +366,7 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
     const bool ok = tile_load(sm, bar, parity, init, mr, mc, UP ? mz : nullptr, g.c0, g.X0, g.Y0, g.t, ta.err, hook);
     if (!ok) return false;
     const int Wc = C.W, WcHc = C.W * C.H;
-    float run[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    float4 run[2] = {zero4(), zero4()};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int item = threadIdx.x + 256 * h;
@@ -292,84 +376,30 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
         const int col = g.c0 + cg * 4;
         if (X >= C.W || Y >= C.H || col >= k) continue;
         const int J = (g.t * C.H + Y) * Wc + X;
-        // value of the smoothed field at tile node (ly, lx)
-        auto sval = [&](int ly, int lx) {
-            const float4 c = cs[ly * TFX + lx];
-            const float4 rv = *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
-            float4 v = (kOmega * fabsf(c.x)) * rv;
+        const auto csm = [&](int ly, int lx) { return cs[ly * TFX + lx]; };
+        const auto rsm = [&](int ly, int lx) {
+            return *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
+        };
+        const auto sval = [&](int ly, int lx) {
+            float4 v = (kOmega * fabsf(csm(ly, lx).x)) * rsm(ly, lx);
             if constexpr (UP)
                 v = fma4(kScale, *reinterpret_cast<const float4 *>(zs + (((ly + 1) >> 1) * TZX + ((lx + 1) >> 1)) * TCB +
                                                                     cg * 4), v);
             return v;
         };
-        auto gval = [&](int j, int dJ) {  // TSV partner on another tier (global memory)
+        const auto vtsv = [&](int j, int i) {  // TSV partner on another tier (global memory)
             const float4 cj = F.coef[j];
             float4 v = (kOmega * fabsf(cj.x)) * f4ld(ta.r + (int64_t)j * k + col);
-            if constexpr (UP) v = fma4(kScale, f4ld(ta.zc + (int64_t)(J + dJ) * k + col), v);
+            if constexpr (UP) v = fma4(kScale, f4ld(ta.zc + (int64_t)(J + (j > i ? WcHc : -WcHc)) * k + col), v);
             return v;
         };
-        float4 acc = zero4();
-        // the smoothed field at the aggregate's own four nodes, computed once: each is the
-        // centre of one stencil and a neighbour in two others (only the ring outside the
-        // aggregate is evaluated per use, once each)
-        const int lx0 = 1 + 2 * ax, ly0 = 1 + 2 * ay;
-        float4 sv[2][2];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) sv[dy][dx] = sval(ly0 + dy, lx0 + dx);
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int x = 2 * X + dx, y = 2 * Y + dy;
-                if (x >= F.W || y >= F.H) continue;
-                const int lx = lx0 + dx, ly = ly0 + dy;
-                const float4 c = cs[ly * TFX + lx];
-                const int i = (g.t * F.H + y) * F.W + x;
-                if (c.x == 0.f) {  // floating node: not in P, z = 0
-                    if constexpr (UP) f4st(ta.out + (int64_t)i * k + col, zero4());
-                    continue;
-                }
-                const float4 ri = *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
-                const float4 vi = sv[dy][dx];
-                float4 gv = c.w * vi;
-                if (c.y != 0.f) gv = fma4(c.y, vi - (dx == 0 ? sv[dy][1] : sval(ly, lx + 1)), gv);
-                {
-                    const float gw = cs[ly * TFX + lx - 1].y;
-                    if (gw != 0.f) gv = fma4(gw, vi - (dx == 1 ? sv[dy][0] : sval(ly, lx - 1)), gv);
-                }
-                if (c.z != 0.f) gv = fma4(c.z, vi - (dy == 0 ? sv[1][dx] : sval(ly + 1, lx)), gv);
-                {
-                    const float gn = cs[(ly - 1) * TFX + lx].z;
-                    if (gn != 0.f) gv = fma4(gn, vi - (dy == 1 ? sv[0][dx] : sval(ly - 1, lx)), gv);
-                }
-                if (c.x < 0.f) {
-                    const int32_t e1 = F.tsv_ptr[i + 1];
-                    for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
-                        const int j = F.tsv_nbr[e];
-                        gv = fma4(F.tsv_g[e], vi - gval(j, j > i ? WcHc : -WcHc), gv);
-                    }
-                }
-                if constexpr (UP) {
-                    const float4 zo = fma4(kOmega * fabsf(c.x), ri - gv, vi);
-                    f4st(ta.out + (int64_t)i * k + col, zo);
-                    if constexpr (DOT) {
-                        run[h][0] = fmaf(ri.x, zo.x, run[h][0]);
-                        run[h][1] = fmaf(ri.y, zo.y, run[h][1]);
-                        run[h][2] = fmaf(ri.z, zo.z, run[h][2]);
-                        run[h][3] = fmaf(ri.w, zo.w, run[h][3]);
-                    }
-                } else {
-                    acc = acc + (ri - gv);
-                }
-            }
+        const float4 acc = mg_agg<UP, DOT>(F, k, g.t, X, Y, ax, ay, col, csm, rsm, sval, vtsv, ta.out, run[h]);
         if constexpr (!UP) f4st(ta.out + (int64_t)J * k + col, acc);
     }
     if constexpr (DOT) {
         // per column: the 64 items of the tile that share it (two per thread), summed in a fixed order
-        const float2 r2[4] = {mg_two_sum(run[0][0], run[1][0]), mg_two_sum(run[0][1], run[1][1]),
-                              mg_two_sum(run[0][2], run[1][2]), mg_two_sum(run[0][3], run[1][3])};
+        const float2 r2[4] = {mg_two_sum(run[0].x, run[1].x), mg_two_sum(run[0].y, run[1].y),
+                              mg_two_sum(run[0].z, run[1].z), mg_two_sum(run[0].w, run[1].w)};
         cta_col_partials(r2, k, g.c0, tile, ta.part);
     }
     return true;
@@ -480,13 +510,13 @@ __device__ __forceinline__ bool mg_dir_body(unsigned char *sm, uint64_t *bar, ui
     if (threadIdx.x < TCB) s_b[threadIdx.x] = g.c0 + (int)threadIdx.x < k ? (float)beta[g.c0 + threadIdx.x] : 0.f;
     __syncthreads();
     if (!ctile_wait(bar, parity, err)) return false;
-    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 run4 = zero4();
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
     const float4 b4 = *reinterpret_cast<const float4 *>(s_b + cg * 4);
     auto sv = [&](int ly, int lx) {
         const int o = (ly * SPX + lx) * TCB + cg * 4;
-        return (b4 * *reinterpret_cast<const float4 *>(ps + o)) + *reinterpret_cast<const float4 *>(zs + o);
+        return fma4v(b4, *reinterpret_cast<const float4 *>(ps + o), *reinterpret_cast<const float4 *>(zs + o));
     };
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
@@ -512,15 +542,15 @@ __device__ __forceinline__ bool mg_dir_body(unsigned char *sm, uint64_t *bar, ui
                 const int32_t e1 = F.tsv_ptr[i + 1];
                 for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
                     const int64_t oj = (int64_t)F.tsv_nbr[e] * k + col;
-                    const float4 d = pv - ((b4 * f4ld(p + oj)) + f4ld(z + oj));
+                    const float4 d = pv - fma4v(b4, f4ld(p + oj), f4ld(z + oj));
                     en = fma4(0.5f * F.tsv_g[e], d * d, en);
                 }
             }
-            run[0] += en.x; run[1] += en.y; run[2] += en.z; run[3] += en.w;
+            run4 = run4 + en;
         }
         f4st(p_out + (int64_t)i * k + col, pv);
     }
-    ctile_partials(run, k, g.c0, tile, part);
+    ctile_partials(run4, k, g.c0, tile, part);
     return true;
 }
 
@@ -534,6 +564,27 @@ __global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ 
     __shared__ __align__(8) uint64_t bar;
     unsigned char *sm = mg_dir_raw + ((128u - (mg_saddr(mg_dir_raw) & 127u)) & 127u);
     mg_dir_body(sm, &bar, 0u, true, (int)blockIdx.x, &mzt, &mpt, &mct, F, k, z, p, beta, p_out, part, err, NoHook{});
+}
+
+// q = G p' at one node in edge form: the pad term, then the east, west, south and north
+// couplings (c.y, gw, c.z, gn; zero where there is no segment), from p' at the node (pv) and
+// at its in-plane neighbours pat(dy, dx).  Every pass that forms r - alpha G p' uses this
+// sequence (and mg_gq_tsv after it), so the values agree bitwise wherever they are formed.
+template <class PA>
+__device__ __forceinline__ float4 mg_gq(float4 c, float gw, float gn, float4 pv, const PA &pat) {
+    float4 q = c.w * pv;
+    if (c.y != 0.f) q = fma4(c.y, pv - pat(0, 1), q);
+    if (gw != 0.f) q = fma4(gw, pv - pat(0, -1), q);
+    if (c.z != 0.f) q = fma4(c.z, pv - pat(1, 0), q);
+    if (gn != 0.f) q = fma4(gn, pv - pat(-1, 0), q);
+    return q;
+}
+// the TSV terms of node i (other tiers; p' read from global memory), in CSR order
+__device__ __forceinline__ float4 mg_gq_tsv(const Lvl &F, int i, int k, int col, const float *__restrict__ p,
+                                            float4 pv, float4 q) {
+    const int32_t e1 = F.tsv_ptr[i + 1];
+    for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) q = fma4(F.tsv_g[e], pv - f4ld(p + (int64_t)F.tsv_nbr[e] * k + col), q);
+    return q;
 }
 
 // r -= alpha G p' with G p' from the staged p' tile of block `blk`; partials of r.D^-1 r; with
@@ -583,10 +634,11 @@ __device__ __forceinline__ bool mg_upd_body(unsigned char *sm, uint64_t *bar, ui
     }
     __syncthreads();
     if (!ctile_wait(bar, parity, err)) return false;
-    float run[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 run4 = zero4();
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
     const float4 a4 = *reinterpret_cast<const float4 *>(s_a + cg * 4);
+    const float4 na4 = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
     const float4 ap4 = XPAIR ? *reinterpret_cast<const float4 *>(s_ap + cg * 4) : zero4();
     auto pv_at = [&](int ly, int lx) {
         return *reinterpret_cast<const float4 *>(ps + (ly * UPX + lx) * TCB + cg * 4);
@@ -602,38 +654,22 @@ __device__ __forceinline__ bool mg_upd_body(unsigned char *sm, uint64_t *bar, ui
         const float4 c = cs[ly * UPX + lx];
         if (c.x == 0.f) continue;  // floating: r, x and p' stay 0
         const float4 pv = pv_at(ly, lx);
-        float4 q = c.w * pv;
-        if (c.y != 0.f) q = fma4(c.y, pv - pv_at(ly, lx + 1), q);
-        {
-            const float gw = cs[ly * UPX + lx - 1].y;
-            if (gw != 0.f) q = fma4(gw, pv - pv_at(ly, lx - 1), q);
-        }
-        if (c.z != 0.f) q = fma4(c.z, pv - pv_at(ly + 1, lx), q);
-        {
-            const float gn = cs[(ly - 1) * UPX + lx].z;
-            if (gn != 0.f) q = fma4(gn, pv - pv_at(ly - 1, lx), q);
-        }
-        if (c.x < 0.f) {
-            const int32_t e1 = F.tsv_ptr[i + 1];
-            for (int32_t e = F.tsv_ptr[i]; e < e1; ++e)
-                q = fma4(F.tsv_g[e], pv - f4ld(p + (int64_t)F.tsv_nbr[e] * k + col), q);
-        }
+        float4 q = mg_gq(c, cs[ly * UPX + lx - 1].y, cs[(ly - 1) * UPX + lx].z, pv,
+                         [&](int dy, int dx) { return pv_at(ly + dy, lx + dx); });
+        if (c.x < 0.f) q = mg_gq_tsv(F, i, k, col, p, pv, q);
         const int64_t o = (int64_t)i * k + col;
-        const float4 rv = f4ld(r + o) - a4 * q;
+        const float4 rv = fma4v(na4, q, f4ld(r + o));
         f4st(r + o, rv);
-        if constexpr (XPAIR) f4st(x + o, f4ld(x + o) + ap4 * f4ld(p_prev + o) + a4 * pv);
+        if constexpr (XPAIR) f4st(x + o, fma4v(a4, pv, fma4v(ap4, f4ld(p_prev + o), f4ld(x + o))));
         const float di = fabsf(c.x);
-        run[0] = fmaf(di * rv.x, rv.x, run[0]);
-        run[1] = fmaf(di * rv.y, rv.y, run[1]);
-        run[2] = fmaf(di * rv.z, rv.z, run[2]);
-        run[3] = fmaf(di * rv.w, rv.w, run[3]);
+        run4 = fma4v(di * rv, rv, run4);
     }
-    ctile_partials(run, k, g.c0, tile, part);
+    ctile_partials(run4, k, g.c0, tile, part);
     return true;
 }
 
 template <bool XPAIR>
-__global__ void __launch_bounds__(256) k_mg_upd_tile(const __grid_constant__ CUtensorMap mpt,
+__global__ void __launch_bounds__(256, 4) k_mg_upd_tile(const __grid_constant__ CUtensorMap mpt,
                                                      const __grid_constant__ CUtensorMap mct, Lvl F, int k,
                                                      const double *__restrict__ alpha,
                                                      const double *__restrict__ alpha_prev,
@@ -873,6 +909,104 @@ static er_status fetch_net(const GridDev &f, HostNet &h) {
 
 // Dense inverse of a (small) level's G in FP64 by Cholesky, G = L L^T, G^-1 = L^-T L^-1,
 // rounded to FP32; rows and columns of floating nodes are zero.
+// A barrier for the host threads of spd_inverse (they spin, yielding, on a generation count).
+struct SpinBarrier {
+    std::atomic<int> count{0}, gen{0};
+    int n = 1;
+    void wait() {
+        const int g = gen.load(std::memory_order_acquire);
+        if (count.fetch_add(1, std::memory_order_acq_rel) + 1 == n) {
+            count.store(0, std::memory_order_relaxed);
+            gen.fetch_add(1, std::memory_order_acq_rel);
+        } else {
+            while (gen.load(std::memory_order_acquire) == g) std::this_thread::yield();
+        }
+    }
+};
+
+// In-place inverse of the symmetric positive definite n x n matrix A (row-major, FP64):
+// blocked right-looking Cholesky A = L L^T (panels of 32 columns: diagonal block, the panel
+// below it, then the trailing lower triangle), the columns of M = L^-1 by forward substitution,
+// and A^-1 = M^T M.  Every inner loop is a dot product over contiguous rows; the rows (columns of
+// M) are shared cyclically among the host threads.  False if A is not positive definite.
+static bool spd_inverse(std::vector<double> &A, int n) {
+    const int NB = 32;
+    int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (n <= 256) nt = 1;
+    std::vector<double> MT((size_t)n * n, 0.0);  // row j: column j of M = L^-1 (entries j .. n-1)
+    std::atomic<bool> bad{false};
+    SpinBarrier bar;
+    bar.n = nt;
+    auto dot = [](const double *x, const double *y, int len) {  // 8 independent partial sums
+        double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int q = 0;
+        for (; q + 8 <= len; q += 8)
+            for (int u = 0; u < 8; ++u) v[u] += x[q + u] * y[q + u];
+        for (; q < len; ++q) v[q & 7] += x[q] * y[q];
+        return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    };
+    auto work = [&](int t) {
+        double *L = A.data();
+        for (int k0 = 0; k0 < n; k0 += NB) {
+            const int k1 = std::min(n, k0 + NB);
+            if (t == 0)  // the diagonal block, already updated by the earlier panels
+                for (int j = k0; j < k1 && !bad.load(); ++j) {
+                    double *lj = L + (size_t)j * n;
+                    const double d = lj[j] - dot(lj + k0, lj + k0, j - k0);
+                    if (!(d > 0.0)) {
+                        bad.store(true);
+                        break;
+                    }
+                    lj[j] = std::sqrt(d);
+                    for (int i = j + 1; i < k1; ++i) {
+                        double *li = L + (size_t)i * n;
+                        li[j] = (li[j] - dot(li + k0, lj + k0, j - k0)) / lj[j];
+                    }
+                }
+            bar.wait();
+            if (bad.load()) return;
+            for (int i = k1 + t; i < n; i += nt) {  // the panel's rows below the block
+                double *li = L + (size_t)i * n;
+                for (int j = k0; j < k1; ++j) {
+                    const double *lj = L + (size_t)j * n;
+                    li[j] = (li[j] - dot(li + k0, lj + k0, j - k0)) / lj[j];
+                }
+            }
+            bar.wait();
+            for (int i = k1 + t; i < n; i += nt) {  // trailing lower triangle
+                double *li = L + (size_t)i * n;
+                for (int j = k1; j <= i; ++j) li[j] -= dot(li + k0, L + (size_t)j * n + k0, k1 - k0);
+            }
+            bar.wait();
+        }
+        for (int j = t; j < n; j += nt) {  // L m = e_j, m zero above j
+            double *m = MT.data() + (size_t)j * n;
+            for (int i = j; i < n; ++i) {
+                const double *li = L + (size_t)i * n;
+                m[i] = ((i == j ? 1.0 : 0.0) - dot(li + j, m + j, i - j)) / li[i];
+            }
+        }
+        bar.wait();
+        for (int a = t; a < n; a += nt)  // (M^T M)_ab = sum over q >= max(a, b) of M_qa M_qb
+            for (int b = a; b < n; ++b) {
+                const double v = dot(MT.data() + (size_t)a * n + b, MT.data() + (size_t)b * n + b, n - b);
+                L[(size_t)a * n + b] = v;
+            }
+        bar.wait();
+        for (int a = t; a < n; a += nt)  // mirror into the lower triangle
+            for (int b = 0; b < a; ++b) L[(size_t)a * n + b] = L[(size_t)b * n + a];
+    };
+    if (nt == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+        work(0);
+        for (auto &x : th) x.join();
+    }
+    return !bad.load();
+}
+
 static er_status dense_inverse(const GridDev &c, std::vector<float> &out) {
     HostNet h;
     er_status st = fetch_net(c, h);
@@ -896,39 +1030,12 @@ static er_status dense_inverse(const GridDev &c, std::vector<float> &out) {
             if (h.tnbr[e] > i) add_edge(i, h.tnbr[e], h.tg[e]);
         for (int32_t e = h.pptr[i]; e < h.pptr[i + 1]; ++e) G[(size_t)i * n + i] += h.pg[e];
     }
-    // Cholesky, lower triangle in place (row-major)
-    for (int j = 0; j < n; ++j) {
-        double d = G[(size_t)j * n + j];
-        for (int q = 0; q < j; ++q) d -= G[(size_t)j * n + q] * G[(size_t)j * n + q];
-        if (!(d > 0.0)) return fail(ER_ERR_INVALID_ARG, "multigrid: coarsest level is not positive definite");
-        const double ljj = std::sqrt(d);
-        G[(size_t)j * n + j] = ljj;
-        for (int i = j + 1; i < n; ++i) {
-            double v = G[(size_t)i * n + j];
-            const double *li = &G[(size_t)i * n], *lj = &G[(size_t)j * n];
-            for (int q = 0; q < j; ++q) v -= li[q] * lj[q];
-            G[(size_t)i * n + j] = v / ljj;
-        }
-    }
-    // M = L^-1 (lower), then G^-1 = M^T M
-    std::vector<double> M((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) {
-        M[(size_t)i * n + i] = 1.0 / G[(size_t)i * n + i];
-        for (int j = 0; j < i; ++j) {
-            double v = 0.0;
-            for (int q = j; q < i; ++q) v += G[(size_t)i * n + q] * M[(size_t)q * n + j];
-            M[(size_t)i * n + j] = -v / G[(size_t)i * n + i];
-        }
-    }
+    // G^-1 = L^-T L^-1 from the Cholesky factor G = L L^T, on the host cores
+    if (!spd_inverse(G, n)) return fail(ER_ERR_INVALID_ARG, "multigrid: coarsest level is not positive definite");
     out.assign((size_t)n * n, 0.0f);
     for (int a = 0; a < n; ++a)
-        for (int b = a; b < n; ++b) {
-            double v = 0.0;
-            for (int q = b; q < n; ++q) v += M[(size_t)q * n + a] * M[(size_t)q * n + b];
-            const float f = (h.fl[a] || h.fl[b]) ? 0.0f : (float)v;
-            out[(size_t)a * n + b] = f;
-            out[(size_t)b * n + a] = f;
-        }
+        for (int b = 0; b < n; ++b)
+            out[(size_t)a * n + b] = (h.fl[a] || h.fl[b]) ? 0.0f : (float)G[(size_t)a * n + b];
     return ER_OK;
 }
 
@@ -1099,15 +1206,18 @@ FoldArgs fold_args(const MgRun &m, int64_t chunks) {
     return f;
 }
 
-// z[0] = V-cycle(r[0]) with the partials of r.z, then the beta fold
+// level l of the hierarchy with this solve's launch order
+Lvl run_lv(const MgRun &m, int l) {
+    Lvl x = m.h->lv[l];
+    x.cb_outer = m.cb_outer;
+    return x;
+}
+
+// z[0] = V-cycle(r0) with the partials of r.z, then the beta fold
 void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     MgHier &h = *m.h;
     const int L = (int)h.lv.size(), k = m.k;
-    auto lv = [&](int l) {  // level l with this solve's launch order
-        Lvl x = h.lv[l];
-        x.cb_outer = m.cb_outer;
-        return x;
-    };
+    auto lv = [&](int l) { return run_lv(m, l); };
     for (int l = 0; l + 1 < L; ++l) {
         const float *rl = l == 0 ? r0 : h.r[l];
         mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_tile<false, false>, tile_grid(h.lv[l + 1], k),
@@ -1359,7 +1469,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
 
 namespace {
 
-constexpr int kBmgLv = 12;          // levels per network (2 x 2 aggregation: 4^11 x 512 nodes)
+constexpr int kBmgLv = 12;          // levels per network (2 x 2 aggregation: 4^11 x 1,024 nodes)
 constexpr int kBmgMaxNets = 1024;   // networks per group: one thread each in the control kernels
 // pass kinds of the work list: 0 .. kBmgLv - 2 the tile pass between levels l and l + 1
 enum { BP_CT = kBmgLv - 1, BP_CINV, BP_N };
@@ -2022,7 +2132,7 @@ er_status mg_batch_solve(er_grid *const *grids, int32_t n, int32_t k, uint64_t s
     for (int q = 0; q < n; ++q) {
         const int c = order[(size_t)q];
         GridDev &g = grids[c]->d;
-        if (g.n > 512 && std::max(g.W, g.H) > 1) {
+        if (g.n > kMgCoarseNodes && std::max(g.W, g.H) > 1) {
             big.push_back(c);
             continue;
         }

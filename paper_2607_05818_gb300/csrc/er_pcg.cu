@@ -451,9 +451,9 @@ er_status solve_locked(er_grid *gg, const void *Yt, void *Z, int32_t k, er_preci
     if (st != ER_OK) return st;
     GridDev &g = gg->d;
     ER_CUDA(cudaSetDevice(g.device));
-    // a grid of at most 512 nodes is the multigrid's coarsest level itself, and 1 x 1 tiers do
+    // a grid of at most kMgCoarseNodes nodes is the multigrid's coarsest level itself, and 1 x 1 tiers do
     // not coarsen: both use Jacobi
-    const bool mg = opt.precond == 1 && g.n > 512 && std::max(g.W, g.H) > 1;
+    const bool mg = opt.precond == 1 && g.n > kMgCoarseNodes && std::max(g.W, g.H) > 1;
     Workspace *wp = nullptr;
     // multigrid: tile_rows sets the finest level's V-cycle rows, not the accurate residual's tiling
     st = get_workspace(&g, k, prec, mg ? 0 : opt.tile_rows, opt.block_order, &wp);
