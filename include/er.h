@@ -201,7 +201,7 @@ er_status er_sketch_cols(er_grid *g, int32_t k_total, int32_t j0, int32_t k_loca
  * aggregates kept, those inside dropped, parallel TSVs and pads of an aggregate merged into
  * one), every level is a grid built like er_grid_create's.  Coarsening stops at the first
  * level of at most 1,024 nodes, which is solved exactly by its dense inverse (FP64 Cholesky on
- * the host cores, stored in FP32); one damped-Jacobi sweep (weight 0.8) runs before and after each
+ * the host cores, stored in FP32); one damped-Jacobi sweep (weight 0.9) runs before and after each
  * coarse correction, so the cycle is a fixed symmetric positive definite operator, as CG
  * needs.  The hierarchy is built on the first such call and cached on the grid.  A grid that
  * does not coarsen to at most 2,048 nodes (too many tiers) returns ER_ERR_INVALID_ARG.  The library allocates (and caches on the grid) its workspace.  opts/stats may be NULL.  Returns ER_ERR_NOT_CONVERGED at

@@ -48,8 +48,8 @@ namespace er {
 
 namespace {
 
-constexpr float kOmega = 0.8f;    // damped-Jacobi weight of the smoother
-constexpr float kScale = 1.6f;    // over-correction of the coarse-grid correction
+constexpr float kOmega = 0.9f;    // damped-Jacobi weight of the smoother (below 1: omega lambda_max(D^-1 G) < 2)
+constexpr float kScale = 1.3f;    // over-correction of the coarse-grid correction
 constexpr int kCoarseTarget = kMgCoarseNodes;  // coarsen until a level has at most this many nodes
 constexpr int kCoarseMax = 2048;     // largest coarsest level (solved by its dense inverse)
 constexpr int kMaxSteps = 16;        // node steps per CTA in the streaming layout
@@ -137,6 +137,7 @@ constexpr int T_R = TFY * TFX * TCB * 4;         // 43,520 bytes
 constexpr int T_C = ((TFY * TFX * 16 + 127) / 128) * 128;
 constexpr int T_Z = TZY * TZX * TCB * 4;         // 13,824 bytes
 constexpr int T_SMEM = T_R + T_C + T_Z + 128;
+constexpr int T_SMEM_DOWN = T_R + T_C + 128;     // the restriction stages no coarse correction
 constexpr uint32_t kTileSpin = 1u << 22;
 
 int64_t n_tiles(const Lvl &C) {
@@ -288,53 +289,47 @@ struct NoHook {
 };
 
 // One item of the tile pass between levels F (finer) and C: aggregate (X, Y) of tier t and the
-// 4 columns from `col`.  The accessors give, at tile-local finer-level node (ly, lx) (the
-// one-node halo included: ly 0 .. TFY-1, lx 0 .. TFX-1), the coefficients csm(ly, lx), the
-// residual rsm(ly, lx) and the smoothed field sval(ly, lx) (w D^-1 r, for UP plus the scaled
-// coarse correction); vtsv(j, i) is the smoothed field at node j, the TSV partner of node i
-// on another tier.  UP: z = v + w D^-1 (r - G v) at the aggregate's four nodes is written to
-// `out` and r.z added to `run`; !UP: returns the restricted residual P^T (r - G v) of the
-// aggregate.  Every path that forms these values calls this function, so they agree bitwise.
+// 4 columns from `col`.  The accessors take a finer-level node by its offset (dy, dx) from the
+// aggregate's first node (-1 .. 2 each: the aggregate's four nodes and the ring around them;
+// after unrolling every offset is a constant, so each shared-memory access is a base address
+// plus an immediate): the coefficients csm(dy, dx), the residual rsm(dy, dx) and the smoothed
+// field sval(dy, dx) (w D^-1 r, for UP plus the scaled coarse correction); vtsv(j, i) is the
+// smoothed field at node j, the TSV partner of node i on another tier.  UP: z = v + w D^-1
+// (r - G v) at the aggregate's four nodes is written to `out` and r.z added to `run`; !UP:
+// returns the restricted residual P^T (r - G v) of the aggregate.  An in-plane coupling that is
+// 0 (no segment, or the mesh edge, where the staged values are 0) adds exactly 0, so no term
+// is skipped.
 template <bool UP, bool DOT, class CS, class RS, class SV, class VT>
-__device__ __forceinline__ float4 mg_agg(const Lvl &F, int k, int t, int X, int Y, int ax, int ay, int col,
-                                         const CS &csm, const RS &rsm, const SV &sval, const VT &vtsv, float *out,
-                                         float4 &run) {
+__device__ __forceinline__ float4 mg_agg(const Lvl &F, int k, int t, int X, int Y, int col, const CS &csm,
+                                         const RS &rsm, const SV &sval, const VT &vtsv, float *out, float4 &run) {
     float4 acc = zero4();
     // the smoothed field at the aggregate's own four nodes, computed once: each is the
     // centre of one stencil and a neighbour in two others (only the ring outside the
     // aggregate is evaluated per use, once each)
-    const int lx0 = 1 + 2 * ax, ly0 = 1 + 2 * ay;
     float4 sv[2][2];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) sv[dy][dx] = sval(ly0 + dy, lx0 + dx);
+        for (int dx = 0; dx < 2; ++dx) sv[dy][dx] = sval(dy, dx);
+    const int64_t i0 = ((int64_t)t * F.H + 2 * Y) * F.W + 2 * X;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) {
-            const int x = 2 * X + dx, y = 2 * Y + dy;
-            if (x >= F.W || y >= F.H) continue;
-            const int lx = lx0 + dx, ly = ly0 + dy;
-            const float4 c = csm(ly, lx);
-            const int i = (t * F.H + y) * F.W + x;
+            if (2 * X + dx >= F.W || 2 * Y + dy >= F.H) continue;
+            const float4 c = csm(dy, dx);
+            const int i = (int)(i0 + (int64_t)dy * F.W + dx);
             if (c.x == 0.f) {  // floating node: not in P, z = 0
                 if constexpr (UP) f4st(out + (int64_t)i * k + col, zero4());
                 continue;
             }
-            const float4 ri = rsm(ly, lx);
+            const float4 ri = rsm(dy, dx);
             const float4 vi = sv[dy][dx];
             float4 gv = c.w * vi;
-            if (c.y != 0.f) gv = fma4(c.y, vi - (dx == 0 ? sv[dy][1] : sval(ly, lx + 1)), gv);
-            {
-                const float gw = csm(ly, lx - 1).y;
-                if (gw != 0.f) gv = fma4(gw, vi - (dx == 1 ? sv[dy][0] : sval(ly, lx - 1)), gv);
-            }
-            if (c.z != 0.f) gv = fma4(c.z, vi - (dy == 0 ? sv[1][dx] : sval(ly + 1, lx)), gv);
-            {
-                const float gn = csm(ly - 1, lx).z;
-                if (gn != 0.f) gv = fma4(gn, vi - (dy == 1 ? sv[0][dx] : sval(ly - 1, lx)), gv);
-            }
+            gv = fma4(c.y, vi - (dx == 0 ? sv[dy][1] : sval(dy, dx + 1)), gv);                // east
+            gv = fma4(csm(dy, dx - 1).y, vi - (dx == 1 ? sv[dy][0] : sval(dy, dx - 1)), gv);  // west
+            gv = fma4(c.z, vi - (dy == 0 ? sv[1][dx] : sval(dy + 1, dx)), gv);                // south
+            gv = fma4(csm(dy - 1, dx).z, vi - (dy == 1 ? sv[0][dx] : sval(dy - 1, dx)), gv);  // north
             if (c.x < 0.f) {
                 const int32_t e1 = F.tsv_ptr[i + 1];
                 for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) gv = fma4(F.tsv_g[e], vi - vtsv(F.tsv_nbr[e], i), gv);
@@ -376,15 +371,20 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
         const int col = g.c0 + cg * 4;
         if (X >= C.W || Y >= C.H || col >= k) continue;
         const int J = (g.t * C.H + Y) * Wc + X;
-        const auto csm = [&](int ly, int lx) { return cs[ly * TFX + lx]; };
-        const auto rsm = [&](int ly, int lx) {
-            return *reinterpret_cast<const float4 *>(rs + (ly * TFX + lx) * TCB + cg * 4);
-        };
-        const auto sval = [&](int ly, int lx) {
-            float4 v = (kOmega * fabsf(csm(ly, lx).x)) * rsm(ly, lx);
-            if constexpr (UP)
-                v = fma4(kScale, *reinterpret_cast<const float4 *>(zs + (((ly + 1) >> 1) * TZX + ((lx + 1) >> 1)) * TCB +
-                                                                    cg * 4), v);
+        // the aggregate's first node is tile node (1 + 2 ay, 1 + 2 ax); its coarse correction
+        // is at (ay + 1, ax + 1) of the coarse tile (one-aggregate halo)
+        const float4 *cb = cs + (1 + 2 * ay) * TFX + (1 + 2 * ax);
+        const float *rb = rs + ((1 + 2 * ay) * TFX + (1 + 2 * ax)) * TCB + cg * 4;
+        const float *zb = zs + ((ay + 1) * TZX + (ax + 1)) * TCB + cg * 4;
+        const auto csm = [&](int dy, int dx) { return cb[dy * TFX + dx]; };
+        const auto rsm = [&](int dy, int dx) { return *reinterpret_cast<const float4 *>(rb + (dy * TFX + dx) * TCB); };
+        const auto sval = [&](int dy, int dx) {
+            float4 v = (kOmega * fabsf(csm(dy, dx).x)) * rsm(dy, dx);
+            if constexpr (UP)  // node offset -1 lies in the aggregate before, 2 in the one after
+                v = fma4(kScale,
+                         *reinterpret_cast<const float4 *>(zb + ((((dy + 2) >> 1) - 1) * TZX + (((dx + 2) >> 1) - 1)) *
+                                                                    TCB),
+                         v);
             return v;
         };
         const auto vtsv = [&](int j, int i) {  // TSV partner on another tier (global memory)
@@ -393,7 +393,7 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
             if constexpr (UP) v = fma4(kScale, f4ld(ta.zc + (int64_t)(J + (j > i ? WcHc : -WcHc)) * k + col), v);
             return v;
         };
-        const float4 acc = mg_agg<UP, DOT>(F, k, g.t, X, Y, ax, ay, col, csm, rsm, sval, vtsv, ta.out, run[h]);
+        const float4 acc = mg_agg<UP, DOT>(F, k, g.t, X, Y, col, csm, rsm, sval, vtsv, ta.out, run[h]);
         if constexpr (!UP) f4st(ta.out + (int64_t)J * k + col, acc);
     }
     if constexpr (DOT) {
@@ -406,7 +406,7 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
 }
 
 template <bool UP, bool DOT>
-__global__ void __launch_bounds__(256, 3) k_mg_tile(const __grid_constant__ CUtensorMap mr,
+__global__ void __launch_bounds__(256, UP ? 3 : 4) k_mg_tile(const __grid_constant__ CUtensorMap mr,
                                                  const __grid_constant__ CUtensorMap mc,
                                                  const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
                                                  const float *__restrict__ r, const float *__restrict__ zc,
@@ -530,13 +530,11 @@ __device__ __forceinline__ bool mg_dir_body(unsigned char *sm, uint64_t *bar, ui
         if (c.x != 0.f) {
             pv = sv(ly, lx);
             float4 en = c.w * (pv * pv);
-            if (c.y != 0.f) {
-                const float4 d = pv - sv(ly, lx + 1);
-                en = fma4(c.y, d * d, en);
-            }
-            if (c.z != 0.f) {
-                const float4 d = pv - sv(ly + 1, lx);
-                en = fma4(c.z, d * d, en);
+            {  // east and south edges (a coupling of 0 adds exactly 0: the staged values are finite)
+                const float4 de = pv - sv(ly, lx + 1);
+                en = fma4(c.y, de * de, en);
+                const float4 ds = pv - sv(ly + 1, lx);
+                en = fma4(c.z, ds * ds, en);
             }
             if (c.x < 0.f) {
                 const int32_t e1 = F.tsv_ptr[i + 1];
@@ -567,16 +565,16 @@ __global__ void __launch_bounds__(256, 4) k_mg_dir_tile(const __grid_constant__ 
 }
 
 // q = G p' at one node in edge form: the pad term, then the east, west, south and north
-// couplings (c.y, gw, c.z, gn; zero where there is no segment), from p' at the node (pv) and
-// at its in-plane neighbours pat(dy, dx).  Every pass that forms r - alpha G p' uses this
-// sequence (and mg_gq_tsv after it), so the values agree bitwise wherever they are formed.
+// couplings (c.y, gw, c.z, gn; 0 where there is no segment, and p' there is a finite staged
+// value, so such a term adds exactly 0), from p' at the node (pv) and at its in-plane
+// neighbours pat(dy, dx); the TSV terms follow (mg_gq_tsv).
 template <class PA>
 __device__ __forceinline__ float4 mg_gq(float4 c, float gw, float gn, float4 pv, const PA &pat) {
     float4 q = c.w * pv;
-    if (c.y != 0.f) q = fma4(c.y, pv - pat(0, 1), q);
-    if (gw != 0.f) q = fma4(gw, pv - pat(0, -1), q);
-    if (c.z != 0.f) q = fma4(c.z, pv - pat(1, 0), q);
-    if (gn != 0.f) q = fma4(gn, pv - pat(-1, 0), q);
+    q = fma4(c.y, pv - pat(0, 1), q);
+    q = fma4(gw, pv - pat(0, -1), q);
+    q = fma4(c.z, pv - pat(1, 0), q);
+    q = fma4(gn, pv - pat(-1, 0), q);
     return q;
 }
 // the TSV terms of node i (other tiers; p' read from global memory), in CSR order
@@ -685,38 +683,60 @@ __global__ void __launch_bounds__(256, 4) k_mg_upd_tile(const __grid_constant__ 
 
 // coarsest level, solved exactly: z = G_c^-1 r with the dense inverse (FP32, symmetric,
 // zero rows and columns at floating nodes) computed once on the host.  A dense product
-// [n_c x ld] x [ld x k]: each CTA owns a 32-row x 32-column tile of z and stages 32 columns
-// of the inverse's rows and 32 rows of r through shared memory at a time; a thread owns
-// one row and 4 columns (two accumulators, even and odd j).  ld % 4 == 0; the inverse's
-// columns n_c .. ld-1 are zero and r has ld rows (rows n_c .. ld-1 zero).
-constexpr int CI_T = 32;
+// [n_c x ld] x [ld x k]: each CTA owns a 32-row x 32-column tile of z.  Per step it stages 128
+// rows of the inverse restricted to the tile's 32 columns (by symmetry, the tile's 32 rows
+// restricted to those 128 columns) and 128 rows of r restricted to the tile's 32 columns; the
+// CTA's four thread groups each take 32 of the 128 (group q: 32 q .. 32 q + 31 of every step)
+// and a thread accumulates a 4 x 4 block of z; the four groups' sums are added in a fixed
+// order at the end.  ld % 4 == 0; the inverse's columns n_c .. ld-1 are zero and r has ld rows
+// (rows n_c .. ld-1 zero).
+constexpr int CI_T = 32, CI_J = 128;
 dim3 cinv_grid(int64_t n, int k) { return dim3((unsigned)((n + CI_T - 1) / CI_T), (unsigned)((k + CI_T - 1) / CI_T)); }
 
 // the tile of row block bx and column block by
 __device__ __forceinline__ void mg_cinv_body(int bx, int by, int n, int ld, int k, const float *__restrict__ ainv,
                                              const float *__restrict__ r, float *__restrict__ z) {
-    __shared__ __align__(16) float As[CI_T][CI_T + 4];  // [row][j], rows padded against bank conflicts
-    __shared__ __align__(16) float Rs[CI_T][CI_T];      // [j][column]
+    __shared__ __align__(16) float As[CI_J][CI_T];  // As[jj][i] = inverse (row0 + i, j0 + jj)
+    __shared__ __align__(16) float Rs[CI_J][CI_T];  // Rs[jj][c] = r (j0 + jj, col0 + c)
     const int row0 = bx * CI_T, col0 = by * CI_T;
-    const int ty = threadIdx.x >> 3, tx = (threadIdx.x & 7) * 4;  // this thread: row ty, columns tx .. tx+3
-    float4 a0 = zero4(), a1 = zero4();
-    for (int j0 = 0; j0 < ld; j0 += CI_T) {
-        {
-            const bool ok = row0 + ty < n && j0 + tx < ld;  // tx doubles as the j offset here
-            *reinterpret_cast<float4 *>(&As[ty][tx]) =
-                ok ? *reinterpret_cast<const float4 *>(ainv + (int64_t)(row0 + ty) * ld + j0 + tx) : zero4();
-            const bool okr = j0 + ty < ld && col0 + tx < k;  // ty doubles as the row of r
-            *reinterpret_cast<float4 *>(&Rs[ty][tx]) = okr ? f4ld(r + (int64_t)(j0 + ty) * k + col0 + tx) : zero4();
+    const int grp = threadIdx.x >> 6, q = threadIdx.x & 63;
+    const int ri = (q >> 3) * 4, ci = (q & 7) * 4;  // this thread: rows ri .. ri+3, columns ci .. ci+3
+    float4 acc[4] = {zero4(), zero4(), zero4(), zero4()};
+    for (int j0 = 0; j0 < ld; j0 += CI_J) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;  // staged row jj = e / 8, 4 values from (e % 8) * 4
+            const int jj = e >> 3, c4 = (e & 7) * 4, j = j0 + jj;
+            const bool oka = j < n && row0 + c4 < ld;
+            const bool okr = j < ld && col0 + c4 < k;
+            *reinterpret_cast<float4 *>(&As[jj][c4]) =
+                oka ? *reinterpret_cast<const float4 *>(ainv + (int64_t)j * ld + row0 + c4) : zero4();
+            *reinterpret_cast<float4 *>(&Rs[jj][c4]) = okr ? f4ld(r + (int64_t)j * k + col0 + c4) : zero4();
         }
         __syncthreads();
-#pragma unroll
-        for (int jj = 0; jj < CI_T; jj += 2) {
-            a0 = fma4(As[ty][jj], *reinterpret_cast<const float4 *>(&Rs[jj][tx]), a0);
-            a1 = fma4(As[ty][jj + 1], *reinterpret_cast<const float4 *>(&Rs[jj + 1][tx]), a1);
+#pragma unroll 8
+        for (int jj = grp * (CI_J / 4); jj < (grp + 1) * (CI_J / 4); ++jj) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[jj][ri]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Rs[jj][ci]);
+            acc[0] = fma4(a.x, b, acc[0]);
+            acc[1] = fma4(a.y, b, acc[1]);
+            acc[2] = fma4(a.z, b, acc[2]);
+            acc[3] = fma4(a.w, b, acc[3]);
         }
         __syncthreads();
     }
-    if (row0 + ty < n && col0 + tx < k) f4st(z + (int64_t)(row0 + ty) * k + col0 + tx, a0 + a1);
+    float4 *red = reinterpret_cast<float4 *>(&As[0][0]);  // groups 1..3: [3][64][4] float4, 12 KiB
+    if (grp > 0)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) red[((grp - 1) * 64 + q) * 4 + u] = acc[u];
+    __syncthreads();
+    if (grp != 0) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float4 s = ((acc[u] + red[q * 4 + u]) + red[(64 + q) * 4 + u]) + red[(128 + q) * 4 + u];
+        const int row = row0 + ri + u;
+        if (row < n && col0 + ci < k) f4st(z + (int64_t)row * k + col0 + ci, s);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_mg_cinv(int n, int ld, int k, const float *__restrict__ ainv,
@@ -1221,7 +1241,7 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     for (int l = 0; l + 1 < L; ++l) {
         const float *rl = l == 0 ? r0 : h.r[l];
         mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_tile<false, false>, tile_grid(h.lv[l + 1], k),
-                  T_SMEM, h.map_r[l], h.map_c[l], h.map_r[l], lv(l), lv(l + 1), k, rl, (const float *)nullptr,
+                  T_SMEM_DOWN, h.map_r[l], h.map_c[l], h.map_r[l], lv(l), lv(l + 1), k, rl, (const float *)nullptr,
                   h.r[l + 1], (float2 *)nullptr, m.err);
     }
     const Lvl &C = h.lv[L - 1];
@@ -1301,7 +1321,8 @@ static er_status mg_prepare(GridDev &g, Workspace &w, MgHier **out) {
         if (ms != ER_OK) return ms;
         static std::atomic<bool> attr{false};  // solves of different grids may run on several threads
         if (!attr.load()) {
-            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T_SMEM_DOWN));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_dir_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM));

@@ -6,7 +6,7 @@ on every level l:
 - restriction r_c = P^T (r - G z0) to the 2 x 2-aggregated network;
 - the coarse correction v = z0 + s P B_c r_c (the coarsest level solved exactly);
 - post-smoothing z = v + omega D^-1 (r - G v),
-with omega = 0.8 and s = 1.6 (an over-correction).
+with omega = 0.9 and s = 1.3 (an over-correction).
 
 This test writes that cycle out in FP64 on dense matrices and forms B column by column
 from unit vectors.  It checks that B is symmetric, that B is positive definite on the
@@ -28,7 +28,7 @@ from paper_2607_05818_gb300 import instances as I
 sys.path.insert(0, os.path.dirname(__file__))
 from mg_rules import aggregate  # noqa: E402
 
-OMEGA, SCALE, COARSEST = 0.8, 1.6, 1024
+OMEGA, SCALE, COARSEST = 0.9, 1.3, 1024
 
 
 def hierarchy(inst, coarsest=COARSEST):
@@ -104,5 +104,5 @@ def test_vcycle_is_spd_and_preconditions(name, make, nlev, coarsest):
     dh = 1.0 / np.sqrt(np.diag(G))
     ev_j = np.linalg.eigvalsh(dh[:, None] * G * dh[None, :])
     kappa_mg, kappa_j = ev_mg.max() / ev_mg.min(), ev_j.max() / ev_j.min()
-    # measured: 4.2, 6.3 and 3.6 against 4,656, 7,320 and 16,410 for Jacobi
+    # measured: 4.1, 5.3 and 3.5 against 4,656, 7,320 and 16,410 for Jacobi
     assert kappa_mg < 20 and kappa_mg * 100 < kappa_j, (kappa_mg, kappa_j)
