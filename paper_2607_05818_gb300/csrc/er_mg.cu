@@ -188,15 +188,16 @@ __device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, uint
         if (mz) mg_tma4(sm + T_R + T_C, mz, bar, c0, X0 - 1, Y0 - 1, t);
         hook();
     }
-    __syncthreads();
-    // every thread waits (bounded); the vote makes the outcome uniform across the CTA
+    // thread 0 waits (bounded) while the other warps wait at the CTA barrier; the vote makes
+    // the outcome uniform, and thread 0's acquire plus the barrier make the data visible
     bool done = true;
-    for (uint32_t spins = 0; !mg_try_wait(bar, parity);) {
-        if (++spins > kTileSpin) {
-            done = false;
-            break;
+    if (threadIdx.x == 0)
+        for (uint32_t spins = 0; !mg_try_wait(bar, parity);) {
+            if (++spins > kTileSpin) {
+                done = false;
+                break;
+            }
         }
-    }
     if (__syncthreads_and(done ? 1 : 0)) return true;
     if (threadIdx.x == 0) {  // raise the error word and let this CTA's own copies land first
         atomicExch(err, 1);
@@ -440,15 +441,20 @@ constexpr int U_SMEM = U_V + U_C + 128;
 int64_t n_ctiles(const Lvl &F) { return (int64_t)((F.W + CX - 1) / CX) * ((F.H + CY - 1) / CY) * F.T; }
 dim3 ctile_grid(const Lvl &F, int k) { return dim3((unsigned)(n_ctiles(F) * ((k + TCB - 1) / TCB))); }
 
-// issue loads (thread 0), then a bounded, CTA-uniform wait
+// After thread 0 issued the tile's loads: a bounded wait, made CTA-uniform.  Thread 0 alone
+// polls the barrier (its acquire, then the CTA barrier, make the copied data visible to every
+// thread); the other warps wait at the CTA barrier without taking issue slots from the
+// co-resident CTAs' arithmetic.  The CTA barrier also publishes the shared values the threads
+// wrote before the call.
 __device__ __forceinline__ bool ctile_wait(uint64_t *bar, uint32_t parity, int *err) {
     bool done = true;
-    for (uint32_t spins = 0; !mg_try_wait(bar, parity);) {
-        if (++spins > kTileSpin) {
-            done = false;
-            break;
+    if (threadIdx.x == 0)
+        for (uint32_t spins = 0; !mg_try_wait(bar, parity);) {
+            if (++spins > kTileSpin) {
+                done = false;
+                break;
+            }
         }
-    }
     if (__syncthreads_and(done ? 1 : 0)) return true;
     if (threadIdx.x == 0) {
         atomicExch(err, 1);
@@ -508,46 +514,51 @@ __device__ __forceinline__ bool mg_dir_body(unsigned char *sm, uint64_t *bar, ui
     }
     __shared__ __align__(16) float s_b[TCB];  // beta in FP32, one conversion per column
     if (threadIdx.x < TCB) s_b[threadIdx.x] = g.c0 + (int)threadIdx.x < k ? (float)beta[g.c0 + threadIdx.x] : 0.f;
-    __syncthreads();
     if (!ctile_wait(bar, parity, err)) return false;
     float4 run4 = zero4();
     const int cg = threadIdx.x & 7;
     const int col = g.c0 + cg * 4;
     const float4 b4 = *reinterpret_cast<const float4 *>(s_b + cg * 4);
-    auto sv = [&](int ly, int lx) {
-        const int o = (ly * SPX + lx) * TCB + cg * 4;
-        return fma4v(b4, *reinterpret_cast<const float4 *>(ps + o), *reinterpret_cast<const float4 *>(zs + o));
+    // this thread: tile column lx, rows 0..3; shared-memory bases so that every access below is
+    // a base plus a constant offset
+    const int lx = threadIdx.x >> 3, x = g.x0 + lx;
+    const float4 *cb = cs + lx;
+    const float *pb = ps + lx * TCB + cg * 4, *zb = zs + lx * TCB + cg * 4;
+    auto sv = [&](int dy, int dx) {
+        const int o = (dy * SPX + dx) * TCB;
+        return fma4v(b4, *reinterpret_cast<const float4 *>(pb + o), *reinterpret_cast<const float4 *>(zb + o));
     };
+    const int i0 = (g.t * F.H + g.y0) * F.W + x;
+    float *po = p_out + (int64_t)i0 * k + col;
+    const int64_t row_k = (int64_t)F.W * k;
+    if (x < F.W && col < k)
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int node = (threadIdx.x >> 3) + 32 * h;  // 0 .. 127
-        const int lx = node % CX, ly = node / CX;
-        const int x = g.x0 + lx, y = g.y0 + ly;
-        if (x >= F.W || y >= F.H || col >= k) continue;
-        const int i = (g.t * F.H + y) * F.W + x;
-        const float4 c = cs[ly * SPX + lx];
-        float4 pv = zero4();
-        if (c.x != 0.f) {
-            pv = sv(ly, lx);
-            float4 en = c.w * (pv * pv);
-            {  // east and south edges (a coupling of 0 adds exactly 0: the staged values are finite)
-                const float4 de = pv - sv(ly, lx + 1);
-                en = fma4(c.y, de * de, en);
-                const float4 ds = pv - sv(ly + 1, lx);
-                en = fma4(c.z, ds * ds, en);
-            }
-            if (c.x < 0.f) {
-                const int32_t e1 = F.tsv_ptr[i + 1];
-                for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
-                    const int64_t oj = (int64_t)F.tsv_nbr[e] * k + col;
-                    const float4 d = pv - fma4v(b4, f4ld(p + oj), f4ld(z + oj));
-                    en = fma4(0.5f * F.tsv_g[e], d * d, en);
+        for (int h = 0; h < 4; ++h) {
+            if (g.y0 + h >= F.H) break;
+            const float4 c = cb[h * SPX];
+            float4 pv = zero4();
+            if (c.x != 0.f) {
+                pv = sv(h, 0);
+                float4 en = c.w * (pv * pv);
+                {  // east and south edges (a coupling of 0 adds exactly 0: the staged values are finite)
+                    const float4 de = pv - sv(h, 1);
+                    en = fma4(c.y, de * de, en);
+                    const float4 ds = pv - sv(h + 1, 0);
+                    en = fma4(c.z, ds * ds, en);
                 }
+                if (c.x < 0.f) {
+                    const int i = i0 + h * F.W;
+                    const int32_t e1 = F.tsv_ptr[i + 1];
+                    for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {
+                        const int64_t oj = (int64_t)F.tsv_nbr[e] * k + col;
+                        const float4 d = pv - fma4v(b4, f4ld(p + oj), f4ld(z + oj));
+                        en = fma4(0.5f * F.tsv_g[e], d * d, en);
+                    }
+                }
+                run4 = run4 + en;
             }
-            run4 = run4 + en;
+            f4st(po + h * row_k, pv);
         }
-        f4st(p_out + (int64_t)i * k + col, pv);
-    }
     ctile_partials(run4, k, g.c0, tile, part);
     return true;
 }
@@ -630,7 +641,6 @@ __device__ __forceinline__ bool mg_upd_body(unsigned char *sm, uint64_t *bar, ui
         s_a[threadIdx.x] = j < k ? (float)alpha[j] : 0.f;
         if constexpr (XPAIR) s_ap[threadIdx.x] = j < k ? (float)alpha_prev[j] : 0.f;
     }
-    __syncthreads();
     if (!ctile_wait(bar, parity, err)) return false;
     float4 run4 = zero4();
     const int cg = threadIdx.x & 7;
@@ -638,30 +648,31 @@ __device__ __forceinline__ bool mg_upd_body(unsigned char *sm, uint64_t *bar, ui
     const float4 a4 = *reinterpret_cast<const float4 *>(s_a + cg * 4);
     const float4 na4 = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
     const float4 ap4 = XPAIR ? *reinterpret_cast<const float4 *>(s_ap + cg * 4) : zero4();
-    auto pv_at = [&](int ly, int lx) {
-        return *reinterpret_cast<const float4 *>(ps + (ly * UPX + lx) * TCB + cg * 4);
-    };
+    // this thread: tile column lx0, rows 0..3 (staged slot (1 + h, 1 + lx0)); shared-memory bases
+    // so that every access below is a base plus a constant offset
+    const int lx0 = threadIdx.x >> 3, xg = g.x0 + lx0;
+    const float4 *cb = cs + UPX + 1 + lx0;
+    const float *pb = ps + (UPX + 1 + lx0) * TCB + cg * 4;
+    auto pv_at = [&](int dy, int dx) { return *reinterpret_cast<const float4 *>(pb + (dy * UPX + dx) * TCB); };
+    const int i0 = (g.t * F.H + g.y0) * F.W + xg;
+    const int64_t o0 = (int64_t)i0 * k + col, row_k = (int64_t)F.W * k;
+    if (xg < F.W && col < k)
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int node = (threadIdx.x >> 3) + 32 * h;
-        const int lx0 = node % CX, ly0 = node / CX;
-        const int xg = g.x0 + lx0, yg = g.y0 + ly0;
-        if (xg >= F.W || yg >= F.H || col >= k) continue;
-        const int lx = lx0 + 1, ly = ly0 + 1;
-        const int i = (g.t * F.H + yg) * F.W + xg;
-        const float4 c = cs[ly * UPX + lx];
-        if (c.x == 0.f) continue;  // floating: r, x and p' stay 0
-        const float4 pv = pv_at(ly, lx);
-        float4 q = mg_gq(c, cs[ly * UPX + lx - 1].y, cs[(ly - 1) * UPX + lx].z, pv,
-                         [&](int dy, int dx) { return pv_at(ly + dy, lx + dx); });
-        if (c.x < 0.f) q = mg_gq_tsv(F, i, k, col, p, pv, q);
-        const int64_t o = (int64_t)i * k + col;
-        const float4 rv = fma4v(na4, q, f4ld(r + o));
-        f4st(r + o, rv);
-        if constexpr (XPAIR) f4st(x + o, fma4v(a4, pv, fma4v(ap4, f4ld(p_prev + o), f4ld(x + o))));
-        const float di = fabsf(c.x);
-        run4 = fma4v(di * rv, rv, run4);
-    }
+        for (int h = 0; h < 4; ++h) {
+            if (g.y0 + h >= F.H) break;
+            const float4 c = cb[h * UPX];
+            if (c.x == 0.f) continue;  // floating: r, x and p' stay 0
+            const float4 pv = pv_at(h, 0);
+            float4 q = mg_gq(c, cb[h * UPX - 1].y, cb[(h - 1) * UPX].z, pv,
+                             [&](int dy, int dx) { return pv_at(h + dy, dx); });
+            if (c.x < 0.f) q = mg_gq_tsv(F, i0 + h * F.W, k, col, p, pv, q);
+            const int64_t o = o0 + h * row_k;
+            const float4 rv = fma4v(na4, q, f4ld(r + o));
+            f4st(r + o, rv);
+            if constexpr (XPAIR) f4st(x + o, fma4v(a4, pv, fma4v(ap4, f4ld(p_prev + o), f4ld(x + o))));
+            const float di = fabsf(c.x);
+            run4 = fma4v(di * rv, rv, run4);
+        }
     ctile_partials(run4, k, g.c0, tile, part);
     return true;
 }
@@ -1710,7 +1721,7 @@ __device__ __forceinline__ void bmg_upd_decode(const BmgNet *__restrict__ nets, 
 
 // r -= alpha G p' (and with XPAIR the paired x update) of every running network (k_mg_upd_tile's body)
 template <bool XPAIR>
-__global__ void __launch_bounds__(256) k_bmg_upd(const BmgNet *__restrict__ nets, const int *__restrict__ list,
+__global__ void __launch_bounds__(256, 4) k_bmg_upd(const BmgNet *__restrict__ nets, const int *__restrict__ list,
                                               int cap, int k, int cur) {
     extern __shared__ unsigned char bmg_upd_raw[];
     __shared__ __align__(8) uint64_t bar;
