@@ -5,6 +5,7 @@
 #include <cuda.h>
 
 #include <chrono>
+#include <utility>
 #include <vector>
 
 #include "er_internal.h"
@@ -284,6 +285,12 @@ struct Prof {
     double ms[ER_N_PASS] = {};
     size_t used = 0;
     std::vector<int> kinds;
+    std::vector<std::pair<int, int>> evs;  // per timed launch: its start and end events in the pool
+    // chained timing (the multigrid solve): a launch that directly follows a timed launch on the
+    // stream starts at that launch's end event, so each launch records one event; any other
+    // stream operation in between breaks the chain (chain = -1)
+    bool chained = false;
+    int chain = -1, pending = -1;
 };
 
 void prof_begin(Workspace &w, Prof *pf, int kind);

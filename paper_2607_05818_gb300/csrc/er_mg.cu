@@ -1356,6 +1356,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
     MgRun m{&g, &w, h, k, tol, Z, w.ints + w.k + w.til.n_colblk, opt.block_order == 2 ? 1 : 0};
     Prof pf;
     pf.on = opt.profile != 0;
+    pf.chained = true;  // one event per timed launch (the stream operations below break the chain)
     const bool use_graph = opt.use_graph && !pf.on;
     ER_CUDA(cudaMemsetAsync(w.ints + w.k + w.til.n_colblk, 0, sizeof(int), w.s));  // error word
     fp32_init(g, w, Yt, Z, tol, &pf);  // r = b, x = 0, p = 0, xhl = 0; rho0 = rho = b.D^-1 b; active
@@ -1376,6 +1377,7 @@ er_status mg_solve_core(GridDev &g, Workspace &w, const void *Yt, void *Z, const
         fp32_accum(g, w, Z, &pf);
         fp32_residual(g, w, Yt, tol, 0, 0, &pf);
         ER_CUDA(cudaMemsetAsync(h->cnt + 1, 0, sizeof(int), w.s));
+        pf.chain = -1;
         prof_begin(w, &pf, ER_PASS_OTHER);
         k_mg_freeze<<<ublocks(k, 128), 128, 0, w.s>>>(k, w.scal + 4 * k, h->msc, tol, w.ints,
                                                        w.scal + 2 * k, h->cnt + 1);

@@ -340,13 +340,22 @@ static cudaEvent_t next_event(Workspace &w, Prof &pf) {
 void prof_begin(Workspace &w, Prof *pf, int kind) {
     if (!pf) return;
     pf->launches[kind]++;
-    if (pf->on) cudaEventRecord(next_event(w, *pf), w.s);
+    if (!pf->on) return;
+    if (pf->chained && pf->chain >= 0) {
+        pf->pending = pf->chain;
+    } else {
+        pf->pending = (int)pf->used;
+        cudaEventRecord(next_event(w, *pf), w.s);
+    }
 }
 
 void prof_end(Workspace &w, Prof *pf, int kind) {
     if (pf && pf->on) {
+        const int e = (int)pf->used;
         cudaEventRecord(next_event(w, *pf), w.s);
         pf->kinds.push_back(kind);
+        pf->evs.emplace_back(pf->pending, e);
+        if (pf->chained) pf->chain = e;
     }
 }
 
@@ -354,10 +363,14 @@ void prof_end(Workspace &w, Prof *pf, int kind) {
 void flush_prof(Workspace &w, Prof &pf) {
     for (size_t i = 0; i < pf.kinds.size(); ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, w.evpool[2 * i], w.evpool[2 * i + 1]) == cudaSuccess) pf.ms[pf.kinds[i]] += ms;
+        if (cudaEventElapsedTime(&ms, w.evpool[(size_t)pf.evs[i].first], w.evpool[(size_t)pf.evs[i].second]) ==
+            cudaSuccess)
+            pf.ms[pf.kinds[i]] += ms;
     }
     pf.kinds.clear();
+    pf.evs.clear();
     pf.used = 0;
+    pf.chain = -1;
 }
 
 template <typename K, typename A>
