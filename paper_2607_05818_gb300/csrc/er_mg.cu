@@ -63,6 +63,11 @@ struct Lvl {  // one level's device arrays (kernel argument)
     const float4 *coef;  // {+-1/d, gE, gS, pad}; sign < 0: the node has TSV segments
     const int32_t *tsv_ptr, *tsv_nbr;
     const float *tsv_g;
+    // TSV segments of the tile pass from this level to the next, grouped by tile (the tiles of
+    // 16 x 4 aggregates): tile q's entries are tent[tent_ptr[q] .. tent_ptr[q + 1]), each
+    // {i, j, aggregate of j, CSR index e}, node by node in CSR order; null where not built
+    const int32_t *tent_ptr;
+    const int4 *tent;
 };
 
 // Thread layout shared by the node-by-RHS kernels: TPN threads per node (one group of 4
@@ -138,6 +143,12 @@ constexpr int T_C = ((TFY * TFX * 16 + 127) / 128) * 128;
 constexpr int T_Z = TZY * TZX * TCB * 4;         // 13,824 bytes
 constexpr int T_SMEM = T_R + T_C + T_Z + 128;
 constexpr int T_SMEM_DOWN = T_R + T_C + 128;     // the restriction stages no coarse correction
+// er_solve's tile passes also stage the TSV partners of up to TCAP segments per tile: per entry
+// {node, g, w/d of the partner} and the partner's row of r (and of the coarse correction, UP)
+constexpr int TCAP = 32;
+constexpr int T_SI = TCAP * 16, T_SR = TCAP * TCB * 4;
+constexpr int T_SMEM_TS = T_R + T_C + T_Z + T_SI + 2 * T_SR + 128;
+constexpr int T_SMEM_DOWN_TS = T_R + T_C + T_SI + T_SR + 128;
 constexpr uint32_t kTileSpin = 1u << 22;
 
 int64_t n_tiles(const Lvl &C) {
@@ -171,10 +182,15 @@ __device__ __forceinline__ bool mg_try_wait(uint64_t *b, uint32_t parity) {
 // `init`: the barrier is initialised here (one tile per CTA); otherwise the caller initialised
 // it once and `parity` is the phase this tile completes (a CTA looping over tiles).  The
 // issuing thread runs `hook` while the copies are in flight.
-template <class Hook>
+// Issue the tile's loads and wait for them.  Returns false (error word raised) on expiry.
+// `init`: the barrier is initialised here (one tile per CTA); otherwise the caller initialised
+// it once and `parity` is the phase this tile completes (a CTA looping over tiles).  The
+// issuing thread runs `hook` while the copies are in flight; warp 1 runs `stage` meanwhile
+// (extra copies on a barrier of their own, and shared values the CTA barrier below publishes).
+template <class Hook, class Stage>
 __device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, uint32_t parity, bool init,
                                           const CUtensorMap *mr, const CUtensorMap *mc, const CUtensorMap *mz, int c0,
-                                          int X0, int Y0, int t, int *err, const Hook &hook) {
+                                          int X0, int Y0, int t, int *err, const Hook &hook, const Stage &stage) {
     if (threadIdx.x == 0) {
         if (init) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar)), "r"(1) : "memory");
@@ -187,6 +203,8 @@ __device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, uint
         mg_tma4(sm + T_R, mc, bar, 0, 2 * X0 - 1, 2 * Y0 - 1, t);
         if (mz) mg_tma4(sm + T_R + T_C, mz, bar, c0, X0 - 1, Y0 - 1, t);
         hook();
+    } else if (threadIdx.x >= 32 && threadIdx.x < 64) {
+        stage();
     }
     // thread 0 waits (bounded) while the other warps wait at the CTA barrier; the vote makes
     // the outcome uniform, and thread 0's acquire plus the barrier make the data visible
@@ -205,6 +223,19 @@ __device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, uint
         }
     }
     return false;
+}
+
+struct NoStage {
+    __device__ void operator()() const {}
+};
+
+// 1-D bulk copy global -> shared completing on `bar` (addresses 16-byte aligned, bytes % 16 == 0)
+__device__ __forceinline__ void mg_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            mg_saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mg_saddr(bar))
+        : "memory");
 }
 
 struct TileGeo {
@@ -294,15 +325,16 @@ struct NoHook {
 // aggregate's first node (-1 .. 2 each: the aggregate's four nodes and the ring around them;
 // after unrolling every offset is a constant, so each shared-memory access is a base address
 // plus an immediate): the coefficients csm(dy, dx), the residual rsm(dy, dx) and the smoothed
-// field sval(dy, dx) (w D^-1 r, for UP plus the scaled coarse correction); vtsv(j, i) is the
-// smoothed field at node j, the TSV partner of node i on another tier.  UP: z = v + w D^-1
+// field sval(dy, dx) (w D^-1 r, for UP plus the scaled coarse correction); tsvt(i, vi, gv) adds
+// the TSV terms of node i, g_e (vi - v_j) for its segments e in CSR order (v_j the smoothed
+// field at the partner j on another tier), to gv.  UP: z = v + w D^-1
 // (r - G v) at the aggregate's four nodes is written to `out` and r.z added to `run`; !UP:
 // returns the restricted residual P^T (r - G v) of the aggregate.  An in-plane coupling that is
 // 0 (no segment, or the mesh edge, where the staged values are 0) adds exactly 0, so no term
 // is skipped.
 template <bool UP, bool DOT, class CS, class RS, class SV, class VT>
 __device__ __forceinline__ float4 mg_agg(const Lvl &F, int k, int t, int X, int Y, int col, const CS &csm,
-                                         const RS &rsm, const SV &sval, const VT &vtsv, float *out, float4 &run) {
+                                         const RS &rsm, const SV &sval, const VT &tsvt, float *out, float4 &run) {
     float4 acc = zero4();
     // the smoothed field at the aggregate's own four nodes, computed once: each is the
     // centre of one stencil and a neighbour in two others (only the ring outside the
@@ -331,10 +363,7 @@ __device__ __forceinline__ float4 mg_agg(const Lvl &F, int k, int t, int X, int 
             gv = fma4(csm(dy, dx - 1).y, vi - (dx == 1 ? sv[dy][0] : sval(dy, dx - 1)), gv);  // west
             gv = fma4(c.z, vi - (dy == 0 ? sv[1][dx] : sval(dy + 1, dx)), gv);                // south
             gv = fma4(csm(dy - 1, dx).z, vi - (dy == 1 ? sv[0][dx] : sval(dy - 1, dx)), gv);  // north
-            if (c.x < 0.f) {
-                const int32_t e1 = F.tsv_ptr[i + 1];
-                for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) gv = fma4(F.tsv_g[e], vi - vtsv(F.tsv_nbr[e], i), gv);
-            }
+            if (c.x < 0.f) gv = tsvt(i, vi, gv);
             if constexpr (UP) {
                 const float4 zo = fma4(kOmega * fabsf(c.x), ri - gv, vi);
                 f4st(out + (int64_t)i * k + col, zo);
@@ -348,18 +377,54 @@ __device__ __forceinline__ float4 mg_agg(const Lvl &F, int k, int t, int X, int 
 
 // prolongation + post-sweep (UP) or pre-sweep + restriction (!UP) over tile block `blk` of the
 // level pair (ta.F, ta.C); false if the wait on the tile's loads expired (error word raised).
-// `ta` may live in shared memory (read where used) or be built from kernel parameters.
-template <bool UP, bool DOT, class TA, class Hook>
+// `ta` may live in shared memory (read where used) or be built from kernel parameters.  TS (one
+// tile per CTA): while the tile is in flight, warp 1 stages the tile's TSV partners (ta.F.tent)
+// by bulk copies on a second barrier `bar2`, and the TSV terms read them from shared memory
+// after waiting on it; a tile with more than TCAP segments, or a level without the table,
+// reads them from global memory.  The values are the same either way.
+template <bool UP, bool DOT, bool TS = false, class TA, class Hook>
 __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, uint32_t parity, bool init, int blk,
                                              const CUtensorMap *mr, const CUtensorMap *mc, const CUtensorMap *mz,
-                                             const TA &ta, int k, const Hook &hook) {
+                                             const TA &ta, int k, const Hook &hook, uint64_t *bar2 = nullptr) {
     const Lvl &F = ta.F, &C = ta.C;
     const float *rs = reinterpret_cast<const float *>(sm);
     const float4 *cs = reinterpret_cast<const float4 *>(sm + T_R);
     const float *zs = reinterpret_cast<const float *>(sm + T_R + T_C);
+    // TS: the staged entries after the tile's regions
+    unsigned char *st = sm + T_R + T_C + (UP ? T_Z : 0);
+    float4 *s_info = reinterpret_cast<float4 *>(st);              // {node i (bits), g, w/d_j, 0}
+    float *s_rr = reinterpret_cast<float *>(st + T_SI);            // partner rows of r
+    float *s_rz = reinterpret_cast<float *>(st + T_SI + T_SR);     // partner rows of the coarse correction
+    __shared__ int s_ne;                                           // staged entries, -1: not staged
     int tile;
     const TileGeo g = tile_geo(C, k, blk, tile);
-    const bool ok = tile_load(sm, bar, parity, init, mr, mc, UP ? mz : nullptr, g.c0, g.X0, g.Y0, g.t, ta.err, hook);
+    const auto stage = [&]() {  // warp 1
+        if constexpr (TS) {
+            const int lane = (int)threadIdx.x - 32;
+            if (lane == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar2)), "r"(1) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            __syncwarp();
+            const int p0 = F.tent_ptr ? F.tent_ptr[tile] : 0, p1 = F.tent_ptr ? F.tent_ptr[tile + 1] : 0;
+            const int ne = F.tent_ptr && p1 - p0 <= TCAP ? p1 - p0 : -1;
+            if (lane == 0) s_ne = ne;
+            if (lane < ne) {
+                const int4 en = F.tent[p0 + lane];  // {i, j, aggregate of j, e}
+                const uint32_t bytes = (uint32_t)(min(TCB, k - g.c0) * 4);
+                asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(mg_saddr(bar2)),
+                             "r"(UP ? 2 * bytes : bytes)
+                             : "memory");
+                mg_bulk(s_rr + lane * TCB, ta.r + (int64_t)en.y * k + g.c0, bytes, bar2);
+                if constexpr (UP) mg_bulk(s_rz + lane * TCB, ta.zc + (int64_t)en.z * k + g.c0, bytes, bar2);
+                s_info[lane] = make_float4(__int_as_float(en.x), F.tsv_g[en.w], kOmega * fabsf(F.coef[en.y].x), 0.f);
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mg_saddr(bar2)) : "memory");
+        }
+    };
+    const bool ok = tile_load(sm, bar, parity, init, mr, mc, UP ? mz : nullptr, g.c0, g.X0, g.Y0, g.t, ta.err, hook,
+                              stage);
     if (!ok) return false;
     const int Wc = C.W, WcHc = C.W * C.H;
     float4 run[2] = {zero4(), zero4()};
@@ -388,15 +453,42 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
                          v);
             return v;
         };
-        const auto vtsv = [&](int j, int i) {  // TSV partner on another tier (global memory)
-            const float4 cj = F.coef[j];
-            float4 v = (kOmega * fabsf(cj.x)) * f4ld(ta.r + (int64_t)j * k + col);
-            if constexpr (UP) v = fma4(kScale, f4ld(ta.zc + (int64_t)(J + (j > i ? WcHc : -WcHc)) * k + col), v);
-            return v;
+        const auto tsvt = [&](int i, float4 vi, float4 gv) {
+            int ne = TS ? s_ne : -1;
+            if (ne > 0) {  // the staged rows have landed (bounded wait; on expiry: global memory)
+                bool ok = false;
+                for (uint32_t q = 0; q < kTileSpin && !(ok = mg_try_wait(bar2, 0u));) ++q;
+                if (!ok) {
+                    atomicExch(ta.err, 1);
+                    ne = -1;
+                }
+            }
+            if (ne >= 0) {  // staged: node i's entries, in CSR order
+                for (int q = 0; q < ne; ++q) {
+                    const float4 in = s_info[q];
+                    if (__float_as_int(in.x) != i) continue;
+                    float4 v = in.z * *reinterpret_cast<const float4 *>(s_rr + q * TCB + cg * 4);
+                    if constexpr (UP) v = fma4(kScale, *reinterpret_cast<const float4 *>(s_rz + q * TCB + cg * 4), v);
+                    gv = fma4(in.y, vi - v, gv);
+                }
+                return gv;
+            }
+            const int32_t e1 = F.tsv_ptr[i + 1];
+            for (int32_t e = F.tsv_ptr[i]; e < e1; ++e) {  // TSV partner on another tier (global memory)
+                const int j = F.tsv_nbr[e];
+                float4 v = (kOmega * fabsf(F.coef[j].x)) * f4ld(ta.r + (int64_t)j * k + col);
+                if constexpr (UP) v = fma4(kScale, f4ld(ta.zc + (int64_t)(J + (j > i ? WcHc : -WcHc)) * k + col), v);
+                gv = fma4(F.tsv_g[e], vi - v, gv);
+            }
+            return gv;
         };
-        const float4 acc = mg_agg<UP, DOT>(F, k, g.t, X, Y, col, csm, rsm, sval, vtsv, ta.out, run[h]);
+        const float4 acc = mg_agg<UP, DOT>(F, k, g.t, X, Y, col, csm, rsm, sval, tsvt, ta.out, run[h]);
         if constexpr (!UP) f4st(ta.out + (int64_t)J * k + col, acc);
     }
+    if constexpr (TS)  // no staged copy may still be landing when the CTA exits
+        if (threadIdx.x == 0 && s_ne > 0)
+            for (uint32_t q = 0; q < kTileSpin && !mg_try_wait(bar2, 0u); ++q) {
+            }
     if constexpr (DOT) {
         // per column: the 64 items of the tile that share it (two per thread), summed in a fixed order
         const float2 r2[4] = {mg_two_sum(run[0].x, run[1].x), mg_two_sum(run[0].y, run[1].y),
@@ -406,17 +498,17 @@ __device__ __forceinline__ bool mg_tile_body(unsigned char *sm, uint64_t *bar, u
     return true;
 }
 
-template <bool UP, bool DOT>
+template <bool UP, bool DOT, bool TS>
 __global__ void __launch_bounds__(256, UP ? 3 : 4) k_mg_tile(const __grid_constant__ CUtensorMap mr,
                                                  const __grid_constant__ CUtensorMap mc,
                                                  const __grid_constant__ CUtensorMap mz, Lvl F, Lvl C, int k,
                                                  const float *__restrict__ r, const float *__restrict__ zc,
                                                  float *__restrict__ out, float2 *part, int *err) {
     extern __shared__ unsigned char mg_tile_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, bar2;
     unsigned char *sm = mg_tile_raw + ((128u - (mg_saddr(mg_tile_raw) & 127u)) & 127u);
     const TileArgs a{F, C, r, zc, out, part, err};
-    mg_tile_body<UP, DOT>(sm, &bar, 0u, true, (int)blockIdx.x, &mr, &mc, &mz, a, k, NoHook{});
+    mg_tile_body<UP, DOT, TS>(sm, &bar, 0u, true, (int)blockIdx.x, &mr, &mc, &mz, a, k, NoHook{}, &bar2);
 }
 
 // ---- TMA-tiled CG passes on the finest level ---------------------------------------------
@@ -878,6 +970,8 @@ struct MgHier {
     // tiled CG passes on the finest level: direction (z, p[0], p[1], coefficients; east/south
     // halo) and update (p[0], p[1], coefficients; halo on every side)
     CUtensorMap dmap_z, dmap_p[2], dmap_c, umap_p[2], umap_c;
+    std::vector<int32_t *> tent_ptr;  // per level: its tile pass's TSV segments grouped by tile
+    std::vector<int4 *> tent;
     float2 *part = nullptr;
     int64_t part_chunks = 0;
     int *cnt = nullptr;            // [0] unconverged columns, [1] active columns
@@ -890,7 +984,51 @@ static Lvl level_of(const GridDev &d) {
     l.cb_outer = 0;
     l.coef = reinterpret_cast<const float4 *>(d.coef32);
     l.tsv_ptr = d.tsv_ptr; l.tsv_nbr = d.tsv_nbr; l.tsv_g = d.tsv_g32;
+    l.tent_ptr = nullptr;
+    l.tent = nullptr;
     return l;
+}
+
+// The TSV segments of level f's nodes grouped by the tile (16 x 4 aggregates of the next level,
+// numbered as the tile passes number them) that holds the node: per tile, node by node in index
+// order, each node's segments in CSR order, as {i, j, aggregate of j, e}.
+static er_status build_tsv_tiles(const GridDev &f, int32_t **ptr_out, int4 **ent_out) {
+    const int64_t n = f.n;
+    const int W = f.W, H = f.H, Wc = (W + 1) / 2, Hc = (H + 1) / 2;
+    const int tx = (Wc + TAX - 1) / TAX, ty = (Hc + TAY - 1) / TAY;
+    const int64_t ntile = (int64_t)tx * ty * f.T;
+    std::vector<int32_t> tp((size_t)n + 1), tn;
+    ER_CUDA(cudaMemcpy(tp.data(), f.tsv_ptr, (size_t)(n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    tn.resize((size_t)tp[(size_t)n]);
+    if (!tn.empty())
+        ER_CUDA(cudaMemcpy(tn.data(), f.tsv_nbr, tn.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    auto tile_of = [&](int64_t i) {
+        const int64_t x = i % W, y = (i / W) % H, t = i / ((int64_t)W * H);
+        return (t * ty + (y / 2) / TAY) * tx + (x / 2) / TAX;
+    };
+    auto agg_of = [&](int64_t j) {
+        const int64_t x = j % W, y = (j / W) % H, t = j / ((int64_t)W * H);
+        return (int32_t)((t * Hc + y / 2) * Wc + x / 2);
+    };
+    std::vector<int32_t> ptr((size_t)ntile + 1, 0);
+    for (int64_t i = 0; i < n; ++i)
+        if (tp[(size_t)i + 1] > tp[(size_t)i]) ptr[(size_t)tile_of(i) + 1] += tp[(size_t)i + 1] - tp[(size_t)i];
+    for (int64_t q = 0; q < ntile; ++q) ptr[(size_t)q + 1] += ptr[(size_t)q];
+    std::vector<int4> ent((size_t)ptr[(size_t)ntile]);
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i) {
+        if (tp[(size_t)i + 1] == tp[(size_t)i]) continue;
+        int32_t &f = fill[(size_t)tile_of(i)];
+        for (int32_t e = tp[(size_t)i]; e < tp[(size_t)i + 1]; ++e) {
+            const int32_t j = tn[(size_t)e];
+            ent[(size_t)f++] = make_int4((int)i, j, agg_of(j), e);
+        }
+    }
+    ER_CUDA(cudaMalloc(ptr_out, ptr.size() * sizeof(int32_t)));
+    ER_CUDA(cudaMemcpy(*ptr_out, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    ER_CUDA(cudaMalloc(ent_out, std::max<size_t>(1, ent.size()) * sizeof(int4)));
+    if (!ent.empty()) ER_CUDA(cudaMemcpy(*ent_out, ent.data(), ent.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    return ER_OK;
 }
 
 void free_mg(GridDev *g) {
@@ -904,6 +1042,8 @@ void free_mg(GridDev *g) {
     if (h->part) cudaFree(h->part);
     if (h->cnt) cudaFree(h->cnt);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
+    for (int32_t *p : h->tent_ptr) cudaFree(p);
+    for (int4 *p : h->tent) cudaFree(p);
     delete h;
     g->mg = nullptr;
 }
@@ -1168,6 +1308,20 @@ static er_status get_mg(GridDev &g, int k, cudaStream_t s, MgHier **out) {
         ER_CUDA(cudaMemcpy(h->ainv, padded.data(), padded.size() * sizeof(float), cudaMemcpyHostToDevice));
         ER_CUDA(cudaMalloc(&h->cnt, 2 * sizeof(int)));
         ER_CUDA(cudaMallocHost(&h->h_cnt, 2 * sizeof(int)));
+        // every tile pass's TSV segments by tile, for the staged partner rows
+        const size_t L = h->lv.size();
+        h->tent_ptr.assign(L - 1, nullptr);
+        h->tent.assign(L - 1, nullptr);
+        for (size_t l = 0; l + 1 < L; ++l) {
+            const GridDev &fl = l == 0 ? g : h->grids[l]->d;
+            er_status ts = build_tsv_tiles(fl, &h->tent_ptr[l], &h->tent[l]);
+            if (ts != ER_OK) {
+                free_mg(&g);
+                return ts;
+            }
+            h->lv[l].tent_ptr = h->tent_ptr[l];
+            h->lv[l].tent = h->tent[l];
+        }
     }
     if (h->k != k) {
         for (size_t i = 1; i < h->r.size(); ++i) cudaFree(h->r[i]);
@@ -1251,9 +1405,16 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     auto lv = [&](int l) { return run_lv(m, l); };
     for (int l = 0; l + 1 < L; ++l) {
         const float *rl = l == 0 ? r0 : h.r[l];
-        mg_launch(*m.w, pf, l == 0 ? ER_PASS_MG_DOWN : ER_PASS_MG, k_mg_tile<false, false>, tile_grid(h.lv[l + 1], k),
-                  T_SMEM_DOWN, h.map_r[l], h.map_c[l], h.map_r[l], lv(l), lv(l + 1), k, rl, (const float *)nullptr,
-                  h.r[l + 1], (float2 *)nullptr, m.err);
+        // the finest level stages its tiles' TSV partners; on the coarse levels, whose launches
+        // are short, the staging's start-up cost outweighed it
+        if (l == 0)
+            mg_launch(*m.w, pf, ER_PASS_MG_DOWN, k_mg_tile<false, false, true>, tile_grid(h.lv[l + 1], k),
+                      T_SMEM_DOWN_TS, h.map_r[l], h.map_c[l], h.map_r[l], lv(l), lv(l + 1), k, rl,
+                      (const float *)nullptr, h.r[l + 1], (float2 *)nullptr, m.err);
+        else
+            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<false, false, false>, tile_grid(h.lv[l + 1], k), T_SMEM_DOWN,
+                      h.map_r[l], h.map_c[l], h.map_r[l], lv(l), lv(l + 1), k, rl, (const float *)nullptr,
+                      h.r[l + 1], (float2 *)nullptr, m.err);
     }
     const Lvl &C = h.lv[L - 1];
     mg_launch(*m.w, pf, ER_PASS_MG, k_mg_cinv, cinv_grid(C.n, k), 0, (int)C.n, h.ld_inv, k, (const float *)h.ainv,
@@ -1261,10 +1422,10 @@ void vcycle(const MgRun &m, const float *r0, Prof *pf) {
     for (int l = L - 2; l >= 0; --l) {
         const float *rl = l == 0 ? r0 : h.r[l];
         if (l == 0)
-            mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_tile<true, true>, tile_grid(h.lv[1], k), T_SMEM, h.map_r[0],
+            mg_launch(*m.w, pf, ER_PASS_MG_UP, k_mg_tile<true, true, true>, tile_grid(h.lv[1], k), T_SMEM_TS, h.map_r[0],
                       h.map_c[0], h.map_z[1], lv(0), lv(1), k, rl, (const float *)h.z[1], h.z[0], h.part, m.err);
         else
-            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<true, false>, tile_grid(h.lv[l + 1], k), T_SMEM, h.map_r[l],
+            mg_launch(*m.w, pf, ER_PASS_MG, k_mg_tile<true, false, false>, tile_grid(h.lv[l + 1], k), T_SMEM, h.map_r[l],
                       h.map_c[l], h.map_z[l + 1], lv(l), lv(l + 1), k, rl, (const float *)h.z[l + 1], h.z[l],
                       (float2 *)nullptr, m.err);
     }
@@ -1332,10 +1493,14 @@ static er_status mg_prepare(GridDev &g, Workspace &w, MgHier **out) {
         if (ms != ER_OK) return ms;
         static std::atomic<bool> attr{false};  // solves of different grids may run on several threads
         if (!attr.load()) {
-            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T_SMEM_DOWN_TS));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          T_SMEM_DOWN));
-            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
-            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T_SMEM));
+            ER_CUDA(cudaFuncSetAttribute(k_mg_tile<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T_SMEM_TS));
             ER_CUDA(cudaFuncSetAttribute(k_mg_dir_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
             ER_CUDA(cudaFuncSetAttribute(k_mg_upd_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM));
