@@ -225,10 +225,6 @@ __device__ __forceinline__ bool tile_load(unsigned char *sm, uint64_t *bar, uint
     return false;
 }
 
-struct NoStage {
-    __device__ void operator()() const {}
-};
-
 // 1-D bulk copy global -> shared completing on `bar` (addresses 16-byte aligned, bytes % 16 == 0)
 __device__ __forceinline__ void mg_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
