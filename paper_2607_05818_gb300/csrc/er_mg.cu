@@ -17,9 +17,9 @@
 //     requires;
 //   * the pre-sweep and restriction are one kernel per level, and prolongation and post-sweep
 //     another: a CTA owns 16 x 4 aggregates (32 x 8 nodes of the finer level) and 32 RHS
-//     columns, staged with a one-node halo by cp.async.bulk.tensor; z0 is never stored, it is
-//     recomputed from r; the coarsest level (at most 1,024 nodes) is solved exactly by its dense
-//     inverse.
+//     columns, staged with a one-node halo by cp.async.bulk.tensor (on the finest level with the
+//     rows of its TSV partners on other tiers too); z0 is never stored, it is recomputed from r;
+//     the coarsest level (at most 1,024 nodes) is solved exactly by its dense inverse.
 // The CG recursion is the FP32 form's (FP32 vectors, double-float dot sums, double-float
 // iterate with the accurate residual substituted every replace_every iterations, and whenever
 // every column's recursive residual meets tol; a column stops only when that accurate residual
